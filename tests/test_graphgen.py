@@ -1,0 +1,93 @@
+"""Generator checks (no GPU): structure, determinism and exact kNN."""
+import numpy as np
+
+import graphgen as gg
+
+
+def _canonical(g):
+    off = g.offsets.astype(np.int64)
+    for v in range(g.n):
+        row = g.indices[off[v]:off[v + 1]]
+        assert np.all(np.diff(row.astype(np.int64)) > 0), "sorted, no duplicates"
+        assert not np.any(row == v), "no self-loops"
+
+
+def _symmetric(g):
+    u = np.repeat(np.arange(g.n, dtype=np.int64), g.degrees())
+    fwd = set(zip(u.tolist(), g.indices.astype(np.int64).tolist()))
+    assert all((b, a) in fwd for a, b in fwd)
+
+
+def test_grid_structure():
+    g = gg.grid(4, 6)
+    assert g.n == 24 and g.m == 2 * (4 * 5 + 3 * 6)
+    _canonical(g)
+    _symmetric(g)
+    deg = g.degrees().reshape(4, 6)
+    assert deg[0, 0] == 2 and deg[0, 3] == 3 and deg[2, 3] == 4
+    s = gg.strip(10)
+    assert s.m == 18 and s.indices[:3].tolist() == [1, 0, 2]
+
+
+def test_dgrid_counts():
+    rows, cols = 30, 20
+    E = rows * (cols - 1) + (rows - 1) * cols
+    both = gg.dgrid(rows, cols, 1, p_both=1.0, shortcuts=0)
+    one = gg.dgrid(rows, cols, 1, p_both=0.0, shortcuts=0)
+    assert both.m == 2 * E and one.m == E
+    h = gg.dgrid(rows, cols, 1)
+    assert h.meta["shortcuts"] == round(1e-4 * gg.dgrid(rows, cols, 1, shortcuts=0).m)
+    g = gg.dgrid(rows, cols, 1, shortcuts=25)
+    base = gg.dgrid(rows, cols, 1, shortcuts=0)
+    assert g.m == base.m + 25
+    _canonical(g)
+    # roughly half the edges kept both ways
+    mid = gg.dgrid(200, 200, 3, shortcuts=0)
+    E2 = 2 * 200 * 199
+    assert abs(mid.m / E2 - 1.5) < 0.01
+
+
+def test_knn_exact_small():
+    npts, k = 400, 5
+    g, xy = gg.knn(npts, k, 7, return_points=True)
+    _canonical(g)
+    _symmetric(g)
+    P = xy.astype(np.float64)
+    d2 = ((P[:, None, :] - P[None, :, :]) ** 2).sum(-1)
+    np.fill_diagonal(d2, np.inf)
+    adj = [set(g.indices[g.offsets[v]:g.offsets[v + 1]].tolist()) for v in range(npts)]
+    for i in range(npts):
+        order = np.lexsort((np.arange(npts), d2[i]))[:k]
+        for j in order:
+            assert j in adj[i] and i in adj[j]
+    # every arc is some point's kNN arc
+    for i in range(npts):
+        for j in adj[i]:
+            ki = set(np.lexsort((np.arange(npts), d2[i]))[:k].tolist())
+            kj = set(np.lexsort((np.arange(npts), d2[j]))[:k].tolist())
+            assert j in ki or i in kj
+
+
+def test_rmat_structure_and_determinism():
+    a = gg.rmat(12, 8, 5)
+    b = gg.rmat(12, 8, 5)
+    c = gg.rmat(12, 8, 6)
+    assert np.array_equal(a.indices, b.indices) and np.array_equal(a.offsets, b.offsets)
+    assert not (a.m == c.m and np.array_equal(a.indices, c.indices))
+    _canonical(a)
+    _symmetric(a)
+    deg = a.degrees()
+    assert deg.max() > 20 * deg[deg > 0].mean()  # skewed
+
+
+def test_pick_sources():
+    g = gg.dgrid(50, 50, 2)
+    s = gg.pick_sources(g, 64, 9)
+    assert len(set(s.tolist())) == 64
+    assert np.all(g.degrees()[s] > 0)
+    assert np.array_equal(s, gg.pick_sources(g, 64, 9))
+
+
+def test_rand_is_counter_based():
+    assert gg.rand(1, 2, 3) == gg.rand(1, 2, 3)
+    assert len({gg.rand(1, 2, i) for i in range(1000)}) == 1000
