@@ -1,0 +1,310 @@
+"""Python binding of the GB300 frontier-traversal library (libpasgal_gb.so).
+
+Argument marshalling only: every step of the traversal runs in the CUDA
+kernels behind the C ABI declared in include/pasgal.h.  PyTorch is used for
+device memory and streams.  There is no CPU fallback: if the shared library
+or a CUDA device is missing, every call raises.
+
+    g = Graph.upload(offsets, indices, directed=False)   # numpy or torch
+    dist = g.bfs(src)                       # torch.int32 view of uint32 on cuda
+    fwd, bwd = g.reach_multi(sources, PG_FWD | PG_BWD)   # torch.int64 views
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpasgal_gb.so")
+
+PG_OK, PG_ERR_INVALID_ARG, PG_ERR_INVALID_GRAPH, PG_ERR_OOM = 0, 1, 2, 3
+PG_ERR_CUDA, PG_ERR_TIMEOUT, PG_ERR_UNSUPPORTED, PG_ERR_OVERFLOW = 4, 5, 6, 7
+STATUS_NAMES = {0: "PG_OK", 1: "PG_ERR_INVALID_ARG", 2: "PG_ERR_INVALID_GRAPH", 3: "PG_ERR_OOM",
+                4: "PG_ERR_CUDA", 5: "PG_ERR_TIMEOUT", 6: "PG_ERR_UNSUPPORTED",
+                7: "PG_ERR_OVERFLOW"}
+PG_DIRECTED, PG_BUILD_TRANSPOSE, PG_SKIP_VALIDATE = 1, 2, 4
+PG_FWD, PG_BWD = 1, 2
+PG_SCHED_FIXED, PG_SCHED_LEARNED, PG_SCHED_RANDOM, PG_SCHED_SCRIPT = 0, 1, 2, 3
+PG_DIR_PUSH, PG_DIR_AUTO = 0, 1
+PG_NUM_ACTIONS, PG_ACTION_PULL = 8, 7
+PG_MLP_NPARAMS = 1512
+INF = 0xFFFFFFFF
+
+# every symbol include/pasgal.h declares
+EXPORTS = ["pg_config_default", "pg_graph_upload", "pg_graph_set_transpose", "pg_graph_free",
+           "pg_graph_info", "pg_bfs", "pg_reach_multi", "pg_bfs_multi", "pg_count_reached",
+           "pg_set_schedule_weights", "pg_mlp_forward", "pg_mlp_backward", "pg_mlp_adam",
+           "pg_autotune", "pg_last_error", "pg_version"]
+
+
+class PgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class RoundTrace(ctypes.Structure):
+    _fields_ = [("round", ctypes.c_uint32), ("action", ctypes.c_uint32),
+                ("frontier", ctypes.c_uint32), ("min_level", ctypes.c_uint32),
+                ("out_edges", ctypes.c_uint64), ("t_begin_ns", ctypes.c_uint64),
+                ("t_end_ns", ctypes.c_uint64), ("settled", ctypes.c_uint64),
+                ("features", ctypes.c_float * 5), ("reserved", ctypes.c_uint32)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("schedule", ctypes.c_uint32),
+                ("tau", ctypes.c_uint32), ("direction", ctypes.c_uint32),
+                ("alpha", ctypes.c_uint32), ("beta", ctypes.c_uint32),
+                ("blocks_per_sm", ctypes.c_uint32), ("threads_per_block", ctypes.c_uint32),
+                ("local_queue", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
+                ("hub_degree", ctypes.c_uint32), ("timeout_ms", ctypes.c_uint32),
+                ("max_rounds", ctypes.c_uint32), ("seed", ctypes.c_uint32),
+                ("script_len", ctypes.c_uint32), ("trace_cap", ctypes.c_uint32),
+                ("test_stall_block", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("script", ctypes.c_void_p), ("trace_out", ctypes.POINTER(RoundTrace)),
+                ("ref_dist", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_uint32), ("pull_rounds", ctypes.c_uint32),
+                ("blocks", ctypes.c_uint32), ("threads", ctypes.c_uint32),
+                ("expansions", ctypes.c_uint64), ("pushes", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load the shared library (build it first with __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: run __graft_entry__.build() (no CPU fallback exists)")
+    lib = ctypes.CDLL(p)
+    vp, u32, u64, sz = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t
+    P = ctypes.POINTER
+    sigs = {
+        "pg_config_default": (None, [P(Config)]),
+        "pg_graph_upload": (ctypes.c_int, [vp, vp, u32, u32, u32, vp, P(vp)]),
+        "pg_graph_set_transpose": (ctypes.c_int, [vp, vp, vp, vp]),
+        "pg_graph_free": (ctypes.c_int, [vp]),
+        "pg_graph_info": (ctypes.c_int, [vp, P(u32), P(u32), P(u32)]),
+        "pg_bfs": (ctypes.c_int, [vp, u32, vp, P(Config), P(Stats), vp]),
+        "pg_reach_multi": (ctypes.c_int, [vp, vp, u32, u32, vp, vp, P(Config), P(Stats), vp]),
+        "pg_bfs_multi": (ctypes.c_int, [vp, vp, u32, vp, P(Config), P(Stats), vp]),
+        "pg_count_reached": (ctypes.c_int, [vp, vp, P(u64), P(u64), vp]),
+        "pg_set_schedule_weights": (ctypes.c_int, [vp, vp, sz]),
+        "pg_mlp_forward": (ctypes.c_int, [vp, vp, u32, vp, vp]),
+        "pg_mlp_backward": (ctypes.c_int, [vp, vp, vp, vp, u32, vp, vp, vp]),
+        "pg_mlp_adam": (ctypes.c_int, [vp, vp, vp, vp, u32, u32, ctypes.c_float, ctypes.c_float,
+                                       ctypes.c_float, ctypes.c_float, vp]),
+        "pg_autotune": (ctypes.c_int, [vp, u32, vp, u32, u32, u32, P(Config), vp]),
+        "pg_last_error": (ctypes.c_char_p, []),
+        "pg_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != PG_OK:
+        raise PgError(rc, load().pg_last_error().decode())
+
+
+def default_config(**kw) -> Config:
+    c = Config()
+    load().pg_config_default(ctypes.byref(c))
+    for k, v in kw.items():
+        if not hasattr(c, k):
+            raise AttributeError(k)
+        setattr(c, k, v)
+    return c
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _u32_array(x):
+    """numpy uint32 view or CUDA tensor -> (pointer, keepalive)."""
+    import torch
+    if isinstance(x, torch.Tensor):
+        if x.dtype not in (torch.int32, torch.uint32) or not x.is_contiguous():
+            raise TypeError("expected a contiguous int32/uint32 tensor")
+        return ctypes.c_void_p(x.data_ptr()), x
+    a = np.ascontiguousarray(x, dtype=np.uint32)
+    return ctypes.c_void_p(a.ctypes.data), a
+
+
+class Graph:
+    """A graph resident on the current CUDA device."""
+
+    def __init__(self, handle, n, m, directed):
+        self._h = handle
+        self.n, self.m, self.directed = n, m, directed
+
+    @classmethod
+    def upload(cls, offsets, indices, directed: bool = False, transpose: bool = True,
+               validate: bool = True, stream=None) -> "Graph":
+        """Copy a CSR (numpy host arrays or CUDA tensors) into library-owned memory."""
+        lib = load()
+        po, ko = _u32_array(offsets)
+        pi, ki = _u32_array(indices)
+        n = int(len(ko)) - 1
+        m = int(len(ki))
+        flags = (PG_DIRECTED if directed else 0) | (PG_BUILD_TRANSPOSE if (directed and transpose) else 0)
+        if not validate:
+            flags |= PG_SKIP_VALIDATE
+        h = ctypes.c_void_p()
+        _check(lib.pg_graph_upload(po, pi, n, m, flags, _stream_ptr(stream), ctypes.byref(h)))
+        return cls(h, n, m, directed)
+
+    @classmethod
+    def from_graphgen(cls, g, **kw) -> "Graph":
+        return cls.upload(g.offsets, g.indices, directed=g.directed, **kw)
+
+    def free(self):
+        if self._h:
+            load().pg_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def info(self):
+        n, m, f = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        _check(load().pg_graph_info(self._h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(f)))
+        return n.value, m.value, f.value
+
+    # ---------------------------------------------------------- traversals
+    def bfs(self, src: int, out=None, cfg: Config | None = None, stats: Stats | None = None,
+            stream=None):
+        """Exact hop distances from src; returns a CUDA int32 tensor (uint32 bits)."""
+        import torch
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        ptr = ctypes.c_void_p(out.data_ptr()) if isinstance(out, torch.Tensor) else \
+            ctypes.c_void_p(out.ctypes.data)
+        _check(load().pg_bfs(self._h, int(src), ptr, ctypes.byref(cfg) if cfg else None,
+                             ctypes.byref(stats) if stats else None, _stream_ptr(stream)))
+        return out
+
+    def bfs_host(self, src: int, out: np.ndarray, cfg: Config | None = None, stream=None):
+        """pg_bfs with a host output buffer (the library stages and copies back)."""
+        assert out.dtype == np.uint32 and out.flags.c_contiguous and len(out) == self.n
+        _check(load().pg_bfs(self._h, int(src), ctypes.c_void_p(out.ctypes.data),
+                             ctypes.byref(cfg) if cfg else None, None, _stream_ptr(stream)))
+        return out
+
+    def reach_multi(self, sources, direction: int = PG_FWD, cfg: Config | None = None,
+                    stats: Stats | None = None, stream=None):
+        """Per-vertex uint64 source bitmasks (int64 CUDA tensors); (fwd, bwd)."""
+        import torch
+        src = np.ascontiguousarray(sources, dtype=np.uint32)
+        fwd = torch.empty(self.n, dtype=torch.int64, device="cuda") if direction & PG_FWD else None
+        bwd = torch.empty(self.n, dtype=torch.int64, device="cuda") if direction & PG_BWD else None
+        _check(load().pg_reach_multi(self._h, ctypes.c_void_p(src.ctypes.data), len(src), direction,
+                                     ctypes.c_void_p(fwd.data_ptr() if fwd is not None else 0),
+                                     ctypes.c_void_p(bwd.data_ptr() if bwd is not None else 0),
+                                     ctypes.byref(cfg) if cfg else None,
+                                     ctypes.byref(stats) if stats else None, _stream_ptr(stream)))
+        return fwd, bwd
+
+    def bfs_multi(self, sources, cfg: Config | None = None, stats: Stats | None = None,
+                  stream=None, out=None):
+        """k x n hop distances (int32 CUDA tensor, uint32 bits), source-major."""
+        import torch
+        src = np.ascontiguousarray(sources, dtype=np.uint32)
+        if out is None:
+            out = torch.empty((len(src), self.n), dtype=torch.int32, device="cuda")
+        _check(load().pg_bfs_multi(self._h, ctypes.c_void_p(src.ctypes.data), len(src),
+                                   ctypes.c_void_p(out.data_ptr()),
+                                   ctypes.byref(cfg) if cfg else None,
+                                   ctypes.byref(stats) if stats else None, _stream_ptr(stream)))
+        return out
+
+    def count_reached(self, dist, stream=None):
+        a, b = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().pg_count_reached(self._h, ctypes.c_void_p(dist.data_ptr()), ctypes.byref(a),
+                                       ctypes.byref(b), _stream_ptr(stream)))
+        return a.value, b.value
+
+    def set_schedule_weights(self, w):
+        a = np.ascontiguousarray(w, dtype=np.float32)
+        _check(load().pg_set_schedule_weights(self._h, ctypes.c_void_p(a.ctypes.data), a.size))
+
+    def autotune(self, sources, kind: int = 0, direction: int = PG_FWD, trials: int = 3,
+                 cfg: Config | None = None, stream=None) -> Config:
+        c = cfg if cfg is not None else default_config()
+        src = np.ascontiguousarray(sources, dtype=np.uint32)
+        _check(load().pg_autotune(self._h, kind, ctypes.c_void_p(src.ctypes.data), len(src),
+                                  direction, trials, ctypes.byref(c), _stream_ptr(stream)))
+        return c
+
+
+def to_uint32(t) -> np.ndarray:
+    """CUDA int32 tensor holding uint32 bits -> numpy uint32."""
+    return t.cpu().numpy().view(np.uint32)
+
+
+def to_uint64(t) -> np.ndarray:
+    return t.cpu().numpy().view(np.uint64)
+
+
+# ------------------------------------------------------------- MLP kernels
+def mlp_forward(params, X, stream=None):
+    import torch
+    Y = torch.empty((X.shape[0], PG_NUM_ACTIONS), dtype=torch.float32, device=X.device)
+    _check(load().pg_mlp_forward(ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(X.data_ptr()),
+                                 X.shape[0], ctypes.c_void_p(Y.data_ptr()), _stream_ptr(stream)))
+    return Y
+
+
+def mlp_backward(params, X, act, target, stream=None):
+    import torch
+    grad = torch.empty(PG_MLP_NPARAMS, dtype=torch.float32, device=X.device)
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    _check(load().pg_mlp_backward(ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(X.data_ptr()),
+                                  ctypes.c_void_p(act.data_ptr()), ctypes.c_void_p(target.data_ptr()),
+                                  X.shape[0], ctypes.c_void_p(grad.data_ptr()),
+                                  ctypes.c_void_p(loss.data_ptr()), _stream_ptr(stream)))
+    return loss, grad
+
+
+def mlp_adam(params, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(load().pg_mlp_adam(ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(grad.data_ptr()),
+                              ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(v.data_ptr()),
+                              params.numel(), t, lr, beta1, beta2, eps, _stream_ptr(stream)))
+
+
+def version() -> str:
+    return load().pg_version().decode()
+
+
+def weights_path() -> str:
+    return os.path.join(_HERE, "schedule_mlp.f32")
+
+
+def trained_weights():
+    """The committed schedule-MLP weights (float32[1512]) or None."""
+    p = weights_path()
+    if not os.path.exists(p):
+        return None
+    w = np.fromfile(p, dtype=np.float32)
+    return w if w.size == PG_MLP_NPARAMS else None

@@ -1,0 +1,202 @@
+// pg_internal.cuh -- internal types and device primitives of the sm_103a
+// traversal library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pasgal.h"
+
+#define PG_INF 0xFFFFFFFFu
+#define PG_NONE 0xFFFFFFFFu
+
+// device status bits (Ctrl::status)
+#define PG_DEV_TIMEOUT 1u
+#define PG_DEV_OVERFLOW 2u
+#define PG_DEV_STALLED 4u
+
+#define PG_NUM_SLOTS 3
+
+// Per-round counters of one frontier bag.  Three of them form a ring: the
+// bag being read (round i), the one being filled (round i + 1) and the one
+// being reset for round i + 2, so no reset ever races with a use.
+struct alignas(128) PgSlot {
+    unsigned size;                 // entries appended to the bag
+    unsigned head;                 // grab cursor over regular entries
+    unsigned hub_cursor;           // grab cursor over concatenated hub edges
+    unsigned min_level;            // min tentative distance pushed (incl. de-duplicated pushes)
+    unsigned long long out_edges;  // sum of out-degrees of appended entries
+    unsigned long long hub_pack;   // (hub count << 40) | hub edge total
+    unsigned long long settled;    // trace: vertices equal to the reference after the round
+    unsigned long long expansions; // vertex expansions during the round that reads this bag
+};
+
+struct alignas(128) PgCtrl {
+    unsigned bar_count;            // grid-barrier arrivals
+    unsigned pad0[31];
+    unsigned bar_gen;              // grid-barrier generation
+    unsigned pad1[31];
+    unsigned status;               // PG_DEV_* bits
+    unsigned rounds;               // rounds executed
+    unsigned pull_rounds;
+    unsigned pad2;
+    unsigned long long t_release;  // %globaltimer when the last barrier opened
+    unsigned long long pushes;
+    unsigned long long expansions;
+    unsigned long long edges_seen; // running sum of out_edges over processed frontiers
+    unsigned pad3[20];
+    PgSlot slot[PG_NUM_SLOTS];
+};
+
+struct PgHub {
+    uint32_t v;      // vertex with out-degree >= hub_degree
+    uint32_t start;  // start of its edges in the concatenated hub-edge space (< 2^40 packed)
+};
+
+// ------------------------------------------------------------ primitives
+
+__device__ __forceinline__ unsigned long long pg_gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned pg_ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned pg_ld_volatile(const unsigned *p) {
+    return *(const volatile unsigned *)p;
+}
+
+__device__ __forceinline__ void pg_st_release(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// L2-coherent load (bypasses the non-coherent L1) for data other SMs update.
+__device__ __forceinline__ uint32_t pg_ldcg(const uint32_t *p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned long long pg_ldcg64(const unsigned long long *p) {
+    return __ldcg(p);
+}
+
+__device__ __forceinline__ unsigned pg_lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Grid-wide barrier for a persistent, co-resident grid.  Every wait is
+// bounded: after `timeout_ns` (or an iteration cap) the waiter sets
+// PG_DEV_TIMEOUT and leaves; a waiter that sees the status already set
+// leaves at once.  Returns false when the traversal must stop.
+// The last arriver stamps Ctrl::t_release before opening the barrier.
+__device__ __forceinline__ bool pg_grid_sync(PgCtrl *c, unsigned nblocks, unsigned &gen,
+                                             unsigned long long timeout_ns, int *s_flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned g = gen;
+        __threadfence();
+        const unsigned prev = atomicAdd(&c->bar_count, 1u);
+        if (prev == nblocks - 1) {
+            atomicExch(&c->bar_count, 0u);
+            *(volatile unsigned long long *)&c->t_release = pg_gtimer();
+            __threadfence();
+            pg_st_release(&c->bar_gen, g + 1);
+        } else {
+            const unsigned long long t0 = pg_gtimer();
+            unsigned long long it = 0;
+            while (pg_ld_acquire(&c->bar_gen) == g) {
+                if ((++it & 31ull) == 0) {
+                    if (pg_ld_volatile(&c->status) != 0u) break;
+                    if (pg_gtimer() - t0 > timeout_ns || it > (1ull << 34)) {
+                        atomicOr(&c->status, PG_DEV_TIMEOUT);
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+        gen = g + 1;
+        *s_flag = (pg_ld_volatile(&c->status) != 0u);
+    }
+    __syncthreads();
+    return *s_flag == 0;
+}
+
+// ------------------------------------------------------------ host side
+
+struct PgGraphDev {
+    const uint32_t *off, *idx;    // forward CSR
+    const uint32_t *toff, *tidx;  // reversed CSR (== forward for undirected)
+    uint32_t n, m;
+};
+
+// Internal helpers shared by the host translation units.
+pg_status pg_set_error(pg_status st, const char *fmt, ...);
+pg_status pg_cuda_error(cudaError_t e, const char *what);
+int pg_device_sms(int dev);
+
+#define PG_CK(call)                                                  \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return pg_cuda_error(e_, #call);      \
+    } while (0)
+
+struct PgMsbfsWork;  // batched BFS buffers (pg_msbfs.cu)
+
+struct pg_graph {
+    int device;
+    uint32_t n, m, flags;
+    bool has_transpose, transpose_is_self;
+    uint32_t *d_off, *d_idx, *d_toff, *d_tidx;
+    // traversal workspace
+    uint32_t *d_bag;      // 2 * bag_cap
+    uint32_t bag_cap;
+    uint32_t *d_stamp;    // 2n round tags (de-duplication)
+    PgHub *d_hubs;        // 2 * hub_cap
+    uint32_t hub_cap;
+    uint32_t hub_degree_alloc;  // hub degree the hub capacity was sized for
+    PgCtrl *d_ctrl;
+    PgCtrl *h_ctrl;       // pinned host copy for status/statistics
+    uint32_t epoch;       // round-tag base for d_stamp
+    void *d_stage;        // staging for host-memory outputs
+    size_t stage_bytes;
+    pg_round_trace *d_trace;
+    uint32_t trace_cap;
+    uint8_t *d_script;
+    uint32_t script_cap;
+    float *d_weights;
+    bool has_weights;
+    PgMsbfsWork *msbfs;
+    int num_sms;
+};
+
+// per-call launch parameters resolved from pg_config
+struct PgLaunch {
+    uint32_t schedule, tau, direction, alpha, beta;
+    uint32_t blocks, threads, qcap, chunk, hub_degree;
+    unsigned long long timeout_ns;
+    uint32_t max_rounds, seed, script_len, trace_cap, stall_block;
+    const uint8_t *script;       // device
+    pg_round_trace *trace;       // device
+    const uint32_t *ref_dist;    // device
+    const float *weights;        // device
+    uint32_t epoch;
+    uint32_t allow_pull;
+};
+
+pg_status pg_resolve_config(pg_graph *g, const pg_config *cfg, PgLaunch *L);
+pg_status pg_stage(pg_graph *g, size_t bytes, void **dev);
+bool pg_is_device_ptr(const void *p);
+pg_status pg_ensure_trace(pg_graph *g, const pg_config *cfg, PgLaunch *L, cudaStream_t s);
+pg_status pg_finish_call(pg_graph *g, const PgLaunch &L, const pg_config *cfg,
+                         pg_stats *stats, cudaStream_t s);
+
+// kernels launched from the API translation unit
+pg_status pg_launch_traverse(pg_graph *g, PgLaunch &L, int kind, uint32_t src,
+                             const uint32_t *sources, uint32_t k, uint32_t dir,
+                             uint32_t *dist, unsigned long long *fwd, unsigned long long *bwd,
+                             cudaStream_t s);
+pg_status pg_launch_msbfs(pg_graph *g, PgLaunch &L, const uint32_t *sources, uint32_t k,
+                          uint32_t *dist, cudaStream_t s);

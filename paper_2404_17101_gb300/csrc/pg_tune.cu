@@ -1,0 +1,117 @@
+// pg_tune.cu -- autotuner for the traversal launch shape.
+//
+// The paper leaves tau tunable (Sec. 2.1); on the GPU the local-queue size,
+// the task chunk, the threads per CTA and the CTAs per SM matter as much.
+// Coordinate descent: for each knob in turn, time every candidate value
+// with the others fixed at the best so far (median of `trials` CUDA-event
+// timed runs) and keep the fastest.  Outputs go to scratch buffers that the
+// tuner allocates and frees itself.
+#include <algorithm>
+#include <vector>
+
+#include "pg_internal.cuh"
+
+namespace {
+
+pg_status time_once(pg_graph *g, uint32_t kind, const uint32_t *sources, uint32_t k, uint32_t dir,
+                    void *out0, void *out1, const pg_config &c, cudaStream_t s, cudaEvent_t e0,
+                    cudaEvent_t e1, float *ms) {
+    PG_CK(cudaEventRecord(e0, s));
+    pg_status st = (kind == 0)
+                       ? pg_bfs(g, sources[0], (uint32_t *)out0, &c, nullptr, s)
+                       : pg_reach_multi(g, sources, k, dir, (uint64_t *)out0, (uint64_t *)out1, &c,
+                                        nullptr, s);
+    if (st) return st;
+    PG_CK(cudaEventRecord(e1, s));
+    PG_CK(cudaEventSynchronize(e1));
+    PG_CK(cudaEventElapsedTime(ms, e0, e1));
+    return PG_OK;
+}
+
+}  // namespace
+
+extern "C" pg_status pg_autotune(pg_graph *g, uint32_t kind, const uint32_t *sources, uint32_t k,
+                                 uint32_t dir, uint32_t trials, pg_config *cfg, void *stream) {
+    if (!g || !sources || !cfg) return pg_set_error(PG_ERR_INVALID_ARG, "NULL argument");
+    if (kind > 1) return pg_set_error(PG_ERR_INVALID_ARG, "kind %u", kind);
+    if (kind == 1 && (k == 0 || k > 64)) return pg_set_error(PG_ERR_INVALID_ARG, "k=%u", k);
+    if (cfg->struct_size != sizeof(pg_config))
+        return pg_set_error(PG_ERR_INVALID_ARG, "pg_config.struct_size mismatch");
+    if (trials == 0) trials = 1;
+    PG_CK(cudaSetDevice(g->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    void *out0 = nullptr, *out1 = nullptr;
+    const size_t bytes = (size_t)g->n * (kind == 0 ? sizeof(uint32_t) : sizeof(uint64_t));
+    PG_CK(cudaMalloc(&out0, bytes));
+    if (kind == 1 && cudaMalloc(&out1, bytes) != cudaSuccess) {
+        cudaFree(out0);
+        return pg_cuda_error(cudaErrorMemoryAllocation, "cudaMalloc(autotune)");
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    pg_config best = *cfg;
+    best.schedule = PG_SCHED_FIXED;
+    best.trace_out = nullptr;
+    best.trace_cap = 0;
+    pg_status st = PG_OK;
+    float best_ms = 1e30f;
+    auto measure = [&](const pg_config &c, float *med) -> pg_status {
+        std::vector<float> t;
+        for (uint32_t i = 0; i < trials; i++) {
+            float ms = 0;
+            pg_status r = time_once(g, kind, sources, k, dir, out0, out1, c, s, e0, e1, &ms);
+            if (r) return r;
+            t.push_back(ms);
+        }
+        std::sort(t.begin(), t.end());
+        *med = t[t.size() / 2];
+        return PG_OK;
+    };
+    // warm-up and baseline
+    st = measure(best, &best_ms);
+    const uint32_t taus[] = {1, 2, 4, 8, 16, 32, 64};
+    const uint32_t chunks[] = {4, 8, 16, 32};
+    const uint32_t queues[] = {128, 512, 2048};
+    const uint32_t threads[] = {256, 512};
+    const uint32_t bps[] = {1, 2, 3, 4};
+    for (int knob = 0; knob < 5 && !st; knob++) {
+        const uint32_t *vals;
+        int nv;
+        switch (knob) {
+            case 0: vals = taus; nv = 7; break;
+            case 1: vals = chunks; nv = 4; break;
+            case 2: vals = queues; nv = 3; break;
+            case 3: vals = threads; nv = 2; break;
+            default: vals = bps; nv = 4; break;
+        }
+        pg_config cur = best;
+        for (int i = 0; i < nv && !st; i++) {
+            pg_config c = best;
+            switch (knob) {
+                case 0: c.tau = vals[i]; break;
+                case 1: c.chunk = vals[i]; break;
+                case 2: c.local_queue = vals[i]; break;
+                case 3: c.threads_per_block = vals[i]; break;
+                default: c.blocks_per_sm = vals[i]; break;
+            }
+            float ms = 0;
+            pg_status r = measure(c, &ms);
+            if (r == PG_ERR_INVALID_ARG) continue;  // shape does not fit: skip
+            if (r) { st = r; break; }
+            if (ms < best_ms) { best_ms = ms; cur = c; }
+        }
+        best = cur;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out0);
+    cudaFree(out1);
+    if (st) return st;
+    cfg->tau = best.tau;
+    cfg->chunk = best.chunk;
+    cfg->local_queue = best.local_queue;
+    cfg->threads_per_block = best.threads_per_block;
+    cfg->blocks_per_sm = best.blocks_per_sm;
+    return PG_OK;
+}

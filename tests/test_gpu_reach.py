@@ -1,0 +1,93 @@
+"""GPU parity tests for pg_reach_multi and pg_bfs_multi (bit-exact).
+
+Reachability masks: bit j of fwd[v] = v reachable from sources[j]; bit j of
+bwd[v] = sources[j] reachable from v (Sec. 2.1).  Batched BFS must equal k
+independent queue BFS runs (Sec. 2.2).
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _reach(pg, G, srcs, direction, **kw):
+    fwd, bwd = G.reach_multi(srcs, direction, cfg=pg.default_config(**kw))
+    return (pg.to_uint64(fwd) if fwd is not None else None,
+            pg.to_uint64(bwd) if bwd is not None else None)
+
+
+def test_tiny_vs_warshall(pg):
+    for seed in range(5):
+        for n, draws, directed in [(1, 1, True), (30, 40, True), (64, 200, True), (50, 60, False)]:
+            g = gg.random_graph(n, draws, directed=directed, seed=seed, keep_raw=True)
+            G = pg.Graph.from_graphgen(g)
+            R = oracle.warshall(g)
+            rng = np.random.default_rng(seed)
+            k = int(rng.integers(1, 65))
+            srcs = rng.integers(0, n, size=k).astype(np.uint32)   # duplicates allowed
+            for tau in (1, 8):
+                f, b = _reach(pg, G, srcs, pg.PG_FWD | pg.PG_BWD, tau=tau)
+                for j, s in enumerate(srcs):
+                    bit = np.uint64(1) << np.uint64(j)
+                    assert np.array_equal((f & bit) != 0, R[s, :]), (seed, n, j)
+                    assert np.array_equal((b & bit) != 0, R[:, s]), (seed, n, j)
+                hi = ~np.uint64(0) << np.uint64(k) if k < 64 else np.uint64(0)
+                assert not np.any(f & hi) and not np.any(b & hi)
+
+
+@pytest.mark.parametrize("tau,kw", [(1, {}), (16, {}), (64, {"chunk": 4}),
+                                     (8, {"hub_degree": 32, "local_queue": 64})])
+def test_dgrid_fwd_bwd(pg, tau, kw):
+    g = gg.dgrid(211, 199, 4)
+    G = pg.Graph.from_graphgen(g)
+    srcs = gg.pick_sources(g, 64, 2)
+    f, b = _reach(pg, G, srcs, pg.PG_FWD | pg.PG_BWD, tau=tau, **kw)
+    assert np.array_equal(f, oracle.reach(g, srcs))
+    assert np.array_equal(b, oracle.reach(g, srcs, backward=True))
+    f1, _ = _reach(pg, G, srcs[:5], pg.PG_FWD, tau=tau)
+    assert np.array_equal(f1, oracle.reach(g, srcs[:5]))
+    _, b1 = _reach(pg, G, srcs[:1], pg.PG_BWD, tau=tau)
+    assert np.array_equal(b1, oracle.reach(g, srcs[:1], backward=True))
+
+
+def test_undirected_reach_is_finite_distance(pg):
+    g = gg.knn(40_000, 2, 6)   # k = 2 leaves many components
+    G = pg.Graph.from_graphgen(g)
+    srcs = gg.pick_sources(g, 64, 3)
+    f, b = _reach(pg, G, srcs, pg.PG_FWD | pg.PG_BWD, tau=16)
+    assert np.array_equal(f, b)
+    D = oracle.bfs_multi(g, srcs)
+    for j in range(64):
+        assert np.array_equal(((f >> np.uint64(j)) & np.uint64(1)) == 1, D[j] != oracle.INF)
+
+
+def test_rmat_hubs(pg):
+    g = gg.rmat(15, 16, 8)
+    G = pg.Graph.from_graphgen(g)
+    srcs = gg.pick_sources(g, 64, 4)
+    f, _ = _reach(pg, G, srcs, pg.PG_FWD, tau=4, hub_degree=128)
+    assert np.array_equal(f, oracle.reach(g, srcs))
+
+
+@pytest.mark.parametrize("make,k", [(lambda: gg.rmat(15, 16, 3), 64), (lambda: gg.knn(50_000, 5, 2), 17),
+                                    (lambda: gg.dgrid(120, 130, 4), 64), (lambda: gg.grid(33, 70), 1)])
+def test_bfs_multi_vs_oracle(pg, make, k):
+    g = make()
+    G = pg.Graph.from_graphgen(g)
+    srcs = gg.pick_sources(g, k, 5)
+    want = oracle.bfs_multi(g, srcs)
+    for direction in (0, 1):
+        st = pg.Stats()
+        D = pg.to_uint32(G.bfs_multi(srcs, cfg=pg.default_config(direction=direction), stats=st))
+        assert np.array_equal(D, want), direction
+
+
+def test_bfs_multi_duplicate_sources(pg):
+    g = gg.knn(5000, 4, 1)
+    G = pg.Graph.from_graphgen(g)
+    srcs = np.array([3, 3, 9, 3], dtype=np.uint32)
+    D = pg.to_uint32(G.bfs_multi(srcs))
+    assert np.array_equal(D, oracle.bfs_multi(g, srcs))
