@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark: exact BFS throughput (GTEPS) and HBM-roofline fraction on one GB300.
+
+Workload (default): single-source BFS from vertex 0 on the kNN graph of
+10,000,000 seeded uniform points in the unit square, k = 5, symmetrised
+(59.6M directed CSR arcs) -- the stand-in for the paper's large-diameter kNN
+inputs (GL5 / CH5, Table 1).  One step = one pg_bfs call (in-kernel init,
+every traversal round, result in HBM).  Two forms are timed on the same
+graph: the plain fixed-tau traversal (tau and launch shape from the
+autotuner) and the learned per-round schedule (when trained weights exist).
+
+Printed: ONE JSON line (rank 0).  `value` is the headline form's GTEPS
+(learned if available, else plain) summed over all ranks (replicas: every
+rank runs the same workload on its own GPU, weak scaling).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BFS GTEPS and % of HBM roofline, learned/batched vs plain on one GB300, exact dist"
+FALLBACK_HBM_GBS = 6800.0
+WORKLOADS = {
+    # name -> (graphgen factory name, source, description)
+    "knn_10m": ("knn_10m", 0, "kNN graph, 10M uniform points in the unit square, k=5, seed 2, "
+                              "symmetrised; BFS from vertex 0"),
+    "grid_1000": ("grid_1000", 0, "1000x1000 undirected 4-neighbour grid; BFS from vertex 0"),
+    "knn_30m_k3": ("knn_30m_k3", 0, "held-out kNN graph, 30M points, k=3, seed 5; BFS from 0"),
+    "strip_20m": ("strip_20m", 0, "1 x 20M strip (path); BFS from vertex 0"),
+}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="knn_10m", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def algorithmic_bytes(n, n_r, m_r):
+    """Bytes an ideal traversal must touch: offsets of reached vertices,
+    their adjacency lists, and one write of every distance."""
+    return 4 * (n_r + 1) + 4 * m_r + 4 * n
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("pg_traverse.cu", "pg_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2404_17101_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", f"traffic_{workload}.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        if d.get("kernel_source_sha256_16") == kernel_source_hash():
+            return float(d["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline_bfs(g, src, budget_s=12.0):
+    """The oracle (serial queue BFS, one core) on the same workload."""
+    import oracle
+    t0 = time.perf_counter()
+    d = oracle.bfs(g, src)
+    t1 = time.perf_counter() - t0
+    reps = max(1, min(20, int(budget_s / max(t1, 1e-3)) - 1))
+    ts = [t1]
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.bfs(g, src)
+        ts.append(time.perf_counter() - t0)
+    n_r, m_r = oracle.reached_edges(g, d)
+    return d, n_r, m_r, ts
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import graphgen as gg
+    import oracle
+    oracle.build()
+    gg.build()
+    fac, src, desc = WORKLOADS[args.workload]
+    g = getattr(gg, fac)()
+    d = oracle.bfs(g, src)
+    n_r, m_r = oracle.reached_edges(g, d)
+    for _ in range(args.warmup):
+        oracle.bfs(g, src)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.bfs(g, src)
+        ts.append(time.perf_counter() - t0)
+    mean = sum(ts) / len(ts)
+    value = m_r / mean / 1e9
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": mean * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "n": g.n, "m": g.m,
+                   "source": src, "reached_vertices": n_r, "traversed_edges": m_r},
+        "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                         "sample": f"full workload, {args.steps} timed serial queue-BFS runs"},
+        "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, world, local = dist_env()
+    import numpy as np
+    import torch
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (no CPU fallback)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import graphgen as gg
+    import paper_2404_17101_gb300 as pg
+
+    fac, src, desc = WORKLOADS[args.workload]
+    g = getattr(gg, fac)()
+    G = pg.Graph.from_graphgen(g)
+    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+
+    # --- forms: plain fixed tau (autotuned) and learned schedule
+    plain_cfg = pg.default_config(tau=16, chunk=8, blocks_per_sm=1)
+    tuned = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        plain_cfg = G.autotune([src], kind=0, trials=3, cfg=plain_cfg)
+        tuned = time.perf_counter() - t0
+    forms = {"plain": plain_cfg}
+    w = pg.trained_weights()
+    if w is not None:
+        G.set_schedule_weights(w)
+        lc = pg.default_config(schedule=pg.PG_SCHED_LEARNED)
+        for f in ("chunk", "local_queue", "threads_per_block", "blocks_per_sm"):
+            setattr(lc, f, getattr(plain_cfg, f))
+        forms["learned"] = lc
+
+    G.bfs(src, out=out, cfg=plain_cfg)
+    n_r, m_r = G.count_reached(out)
+    B = algorithmic_bytes(g.n, n_r, m_r)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")  # 256 MB > L2
+
+    def timed(cfg, steps, warmup, sampler=None):
+        st = pg.Stats()
+        for _ in range(warmup):
+            G.bfs(src, out=out, cfg=cfg, stats=st)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        if sampler:
+            sampler.start()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        kms, rounds, exps = [], [], []
+        for i in range(steps):
+            flush.fill_(i)                      # L2 flush between steps, outside the events
+            ev[i][0].record()
+            G.bfs(src, out=out, cfg=cfg, stats=st)
+            ev[i][1].record()
+            kms.append(st.kernel_ms)
+            rounds.append(st.rounds)
+            exps.append(st.expansions)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        clocks = sampler.stop() if sampler else None
+        ms = [a.elapsed_time(b) for a, b in ev]
+        total = torch.tensor([sum(ms)], dtype=torch.float64, device="cuda")
+        if dist:
+            dist.all_reduce(total, op=dist.ReduceOp.MAX)
+        return {"ms": ms, "total_ms_max": float(total.item()), "kernel_ms": kms,
+                "rounds": rounds, "expansions": exps, "clocks": clocks}
+
+    results = {}
+    for name, cfg in forms.items():
+        sampler = ClockSampler(local) if name == ("learned" if "learned" in forms else "plain") else None
+        results[name] = timed(cfg, args.steps, args.warmup, sampler)
+    head = "learned" if "learned" in forms else "plain"
+    R = results[head]
+    ms_per_step = R["total_ms_max"] / args.steps
+    value = world * m_r * args.steps / (R["total_ms_max"] * 1e6)
+    peak, peak_kind = measured_peak()
+    kmean = statistics.mean(R["kernel_ms"])
+    achieved = B / (kmean * 1e-3) / 1e9
+    traffic = profiled_traffic(args.workload)
+
+    # exactness on this run's output, checked against the oracle in the CPU leg
+    cpu = None
+    exact = None
+    if rank == 0 and not args.no_cpu_baseline:
+        d_or, nr_o, mr_o, ts = cpu_baseline_bfs(g, src)
+        exact = bool(np.array_equal(pg.to_uint32(out), d_or))
+        med = statistics.median(ts)
+        cpu = {"value": mr_o / med / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+               "sample": f"full workload (n={g.n}, m={g.m}), {len(ts)} serial queue-BFS runs, "
+                         f"median {med*1e3:.1f} ms"}
+
+    # end to end through the C ABI with host buffers: upload from pinned host
+    # memory, BFS, distances back into pinned host memory, free
+    e2e = None
+    if not args.no_e2e:
+        off_h = torch.from_numpy(g.offsets.view(np.int32)).pin_memory()
+        idx_h = torch.from_numpy(g.indices.view(np.int32)).pin_memory()
+        dist_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
+        lib = pg.load()
+        import ctypes
+        cfg = forms[head]
+        ts = []
+        nsteps = max(1, min(args.steps, 5))
+        for i in range(nsteps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = ctypes.c_void_p()
+            pg._check(lib.pg_graph_upload(ctypes.c_void_p(off_h.data_ptr()),
+                                          ctypes.c_void_p(idx_h.data_ptr()), g.n, g.m, 0,
+                                          pg._stream_ptr(), ctypes.byref(h)))
+            if head == "learned":
+                pg._check(lib.pg_set_schedule_weights(h, ctypes.c_void_p(w.ctypes.data), w.size))
+            pg._check(lib.pg_bfs(h, src, ctypes.c_void_p(dist_h.data_ptr()), ctypes.byref(cfg), None,
+                                 pg._stream_ptr()))
+            pg._check(lib.pg_graph_free(h))
+            t1 = time.perf_counter()
+            if i > 0:
+                ts.append(t1 - t0)
+        emean = sum(ts) / len(ts)
+        e2e = {"value": world * m_r / emean / 1e9, "unit": "GTEPS",
+               "h2d_bytes_per_step": 4 * (g.n + 1) + 4 * g.m,
+               "d2h_bytes_per_step": 4 * g.n, "steps": nsteps,
+               "ms_per_step": emean * 1e3}
+
+    if rank == 0:
+        def summary(r):
+            return {"gteps": m_r * len(r["ms"]) / (sum(r["ms"]) * 1e6),
+                    "ms_per_step": sum(r["ms"]) / len(r["ms"]),
+                    "kernel_ms_mean": statistics.mean(r["kernel_ms"]),
+                    "rounds_mean": statistics.mean(r["rounds"]),
+                    "expansions_per_reached": statistics.mean(r["expansions"]) / max(n_r, 1)}
+        cfgd = lambda c: {f: int(getattr(c, f)) for f in ("schedule", "tau", "chunk", "local_queue",
+                                                          "threads_per_block", "blocks_per_sm")}
+        line = {
+            "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "n": g.n, "m": g.m,
+                       "source": src, "reached_vertices": n_r, "traversed_edges": m_r,
+                       "headline_form": head, "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"replicas x{world}", "forms": {k: cfgd(c) for k, c in forms.items()},
+                       "autotune_s": tuned},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "pg_traverse_kernel<BFS>", "algorithmic_bytes": B,
+                         "kernel_ms_mean": kmean},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": R["clocks"],
+            "exact_vs_oracle": exact,
+            "forms": {k: summary(v) for k, v in results.items()},
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

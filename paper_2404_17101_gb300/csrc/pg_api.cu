@@ -1,6 +1,7 @@
 // pg_api.cu -- host side of the C ABI: errors, graph upload (validation,
 // transpose), configuration, workspace, and the traversal entry points.
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -268,6 +269,80 @@ static pg_status build_transpose(pg_graph *g, cudaStream_t s) {
     return PG_OK;
 }
 
+// Degree statistics: cnt[0..2] = #vertices with degree > 4, > 8, > 16;
+// cnt[3] = largest degree.
+__global__ void k_deg_stats(const uint32_t *off, uint32_t n, unsigned *cnt) {
+    unsigned a = 0, b = 0, c = 0, mx = 0;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const uint32_t d = off[v + 1] - off[v];
+        a += d > 4; b += d > 8; c += d > 16;
+        mx = max(mx, d);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+        b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
+        c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+        mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (a) atomicAdd(cnt, a);
+        if (b) atomicAdd(cnt + 1, b);
+        if (c) atomicAdd(cnt + 2, c);
+        atomicMax(cnt + 3, mx);
+    }
+}
+
+// Padded rows: row v holds v's neighbours then 0xFFFFFFFF padding, or
+// PG_ELL_LONG in every slot when v has more than W neighbours.
+__global__ void k_build_ell(const uint32_t *off, const uint32_t *idx, uint32_t n, uint32_t W,
+                            uint32_t *ell) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const uint32_t b = off[v], d = off[v + 1] - b;
+        uint32_t *row = ell + (size_t)v * W;
+        if (d > W) {
+            for (uint32_t j = 0; j < W; j++) row[j] = PG_ELL_LONG;
+        } else {
+            for (uint32_t j = 0; j < W; j++) row[j] = (j < d) ? idx[b + j] : PG_NONE;
+        }
+    }
+}
+
+// Degree statistics of one direction; builds its padded rows when they fit.
+static pg_status build_rows(pg_graph *g, int which, bool allow, cudaStream_t s) {
+    const uint32_t *off = which ? g->d_toff : g->d_off;
+    const uint32_t *idx = which ? g->d_tidx : g->d_idx;
+    unsigned *cnt = nullptr;
+    PG_CK(cudaMallocAsync(&cnt, 4 * sizeof(unsigned), s));
+    PG_CK(cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned), s));
+    k_deg_stats<<<g->num_sms * 4, 256, 0, s>>>(off, g->n, cnt);
+    unsigned h[4];
+    PG_CK(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PG_CK(cudaStreamSynchronize(s));
+    PG_CK(cudaFreeAsync(cnt, s));
+    g->maxdeg[which] = h[3];
+    g->d_ell[which] = nullptr;
+    g->ellw[which] = 0;
+    if (!allow) return PG_OK;
+    const uint64_t tol = g->n / 1000;
+    uint32_t W = 0;
+    if (h[0] <= tol) W = 4;
+    else if (h[1] <= tol) W = 8;
+    else if (h[2] <= tol) W = 16;
+    if (!W) return PG_OK;
+    uint32_t *ell = nullptr;
+    if (cudaMalloc(&ell, (size_t)g->n * W * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();  // no room: CSR only
+        return PG_OK;
+    }
+    k_build_ell<<<g->num_sms * 8, 256, 0, s>>>(off, idx, g->n, W, ell);
+    PG_CK(cudaGetLastError());
+    g->d_ell[which] = ell;
+    g->ellw[which] = W;
+    return PG_OK;
+}
+
 static pg_status copy_in(uint32_t *dst, const uint32_t *src, size_t count, cudaStream_t s) {
     if (count == 0) return PG_OK;
     const cudaMemcpyKind kind = pg_is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -295,6 +370,8 @@ static pg_status validate(pg_graph *g, const uint32_t *off, const uint32_t *idx,
 
 static void release(pg_graph *g) {
     if (!g) return;
+    if (g->d_ell[1] && g->d_ell[1] != g->d_ell[0]) cudaFree(g->d_ell[1]);
+    cudaFree(g->d_ell[0]);
     cudaFree(g->d_off);
     cudaFree(g->d_idx);
     if (!g->transpose_is_self) {
@@ -310,6 +387,8 @@ static void release(pg_graph *g) {
     cudaFree(g->d_trace);
     cudaFree(g->d_script);
     cudaFree(g->d_weights);
+    if (g->ev0) cudaEventDestroy(g->ev0);
+    if (g->ev1) cudaEventDestroy(g->ev1);
     extern void pg_msbfs_release(pg_graph *);
     pg_msbfs_release(g);
     delete g;
@@ -369,7 +448,22 @@ extern "C" pg_status pg_graph_upload(const uint32_t *offsets, const uint32_t *in
         g->has_transpose = true;
         g->transpose_is_self = true;
     }
+    PG_TRY(build_rows(g, 0, !(flags & PG_NO_ELL), s));
+    if (g->has_transpose) {
+        if (g->transpose_is_self) {
+            g->d_ell[1] = g->d_ell[0];
+            g->ellw[1] = g->ellw[0];
+            g->maxdeg[1] = g->maxdeg[0];
+        } else {
+            PG_TRY(build_rows(g, 1, !(flags & PG_NO_ELL), s));
+        }
+    }
     PG_TRY(alloc_workspace(g, 2048, s));
+    {
+        cudaError_t e = cudaEventCreate(&g->ev0);
+        if (e == cudaSuccess) e = cudaEventCreate(&g->ev1);
+        if (e != cudaSuccess) { release(g); return pg_cuda_error(e, "cudaEventCreate"); }
+    }
     {
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { release(g); return pg_cuda_error(e, "upload"); }
@@ -396,10 +490,16 @@ extern "C" pg_status pg_graph_set_transpose(pg_graph *g, const uint32_t *t_offse
     if (!st) st = validate(g, toff, tidx, g->n, g->m, s);
     if (st) { cudaFree(toff); cudaFree(tidx); return st; }
     if (!g->transpose_is_self) { cudaFree(g->d_toff); cudaFree(g->d_tidx); }
+    if (g->d_ell[1] && g->d_ell[1] != g->d_ell[0]) cudaFree(g->d_ell[1]);
+    g->d_ell[1] = nullptr;
+    g->ellw[1] = 0;
     g->d_toff = toff;
     g->d_tidx = tidx;
     g->has_transpose = true;
     g->transpose_is_self = false;
+    st = build_rows(g, 1, !(g->flags & PG_NO_ELL), s);
+    if (st) return st;
+    PG_CK(cudaStreamSynchronize(s));
     return PG_OK;
 }
 
@@ -435,7 +535,10 @@ extern "C" pg_status pg_set_schedule_weights(pg_graph *g, const float *w, size_t
 
 pg_status pg_finish_call(pg_graph *g, const PgLaunch &L, const pg_config *cfg, pg_stats *stats,
                          cudaStream_t s) {
-    PG_CK(cudaMemcpyAsync(g->h_ctrl, g->d_ctrl, sizeof(PgCtrl), cudaMemcpyDeviceToHost, s));
+    // status, counters and slots only (the barrier flags are not needed)
+    const size_t off = offsetof(PgCtrl, status);
+    PG_CK(cudaMemcpyAsync((char *)g->h_ctrl + off, (const char *)g->d_ctrl + off, sizeof(PgCtrl) - off,
+                          cudaMemcpyDeviceToHost, s));
     PG_CK(cudaStreamSynchronize(s));
     const PgCtrl &c = *g->h_ctrl;
     // advance the round-tag epoch past every tag this call used
@@ -453,6 +556,13 @@ pg_status pg_finish_call(pg_graph *g, const PgLaunch &L, const pg_config *cfg, p
         stats->threads = L.threads;
         stats->expansions = c.expansions;
         stats->pushes = c.pushes;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, g->ev0, g->ev1) != cudaSuccess) {
+            cudaGetLastError();
+            ms = 0.f;
+        }
+        stats->kernel_ms = ms;
+        stats->reserved = 0;
     }
     if (cfg && cfg->trace_out && cfg->trace_cap && L.trace) {
         const uint32_t nrec = c.rounds < cfg->trace_cap ? c.rounds : cfg->trace_cap;
@@ -460,6 +570,9 @@ pg_status pg_finish_call(pg_graph *g, const PgLaunch &L, const pg_config *cfg, p
             PG_CK(cudaMemcpy(cfg->trace_out, L.trace, (size_t)nrec * sizeof(pg_round_trace),
                              cudaMemcpyDeviceToHost));
     }
+    if (c.dbg_site)
+        return pg_set_error(PG_ERR_CUDA, "bounds check: site %u saw id 0x%08x (round %u)", c.dbg_site,
+                            c.dbg_value, c.dbg_round);
     if (c.status & PG_DEV_TIMEOUT)
         return pg_set_error(PG_ERR_TIMEOUT, "device wait exceeded %llu ms (round %u)",
                             L.timeout_ns / 1000000ull, c.rounds);

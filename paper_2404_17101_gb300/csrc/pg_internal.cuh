@@ -24,26 +24,30 @@ struct alignas(128) PgSlot {
     unsigned head;                 // grab cursor over regular entries
     unsigned hub_cursor;           // grab cursor over concatenated hub edges
     unsigned min_level;            // min tentative distance pushed (incl. de-duplicated pushes)
+    unsigned max_level;            // max tentative distance pushed
     unsigned long long out_edges;  // sum of out-degrees of appended entries
     unsigned long long hub_pack;   // (hub count << 40) | hub edge total
     unsigned long long settled;    // trace: vertices equal to the reference after the round
     unsigned long long expansions; // vertex expansions during the round that reads this bag
+    unsigned pad[2];
 };
 
+#define PG_ELL_LONG 0xFFFFFFFEu  // padded-row marker: the vertex's list is in the CSR
+
 struct alignas(128) PgCtrl {
-    unsigned bar_count;            // grid-barrier arrivals
+    unsigned bar_cnt;              // grid-barrier arrivals (monotone, wraps)
     unsigned pad0[31];
-    unsigned bar_gen;              // grid-barrier generation
-    unsigned pad1[31];
     unsigned status;               // PG_DEV_* bits
     unsigned rounds;               // rounds executed
     unsigned pull_rounds;
-    unsigned pad2;
-    unsigned long long t_release;  // %globaltimer when the last barrier opened
+    unsigned pad1;
     unsigned long long pushes;
     unsigned long long expansions;
-    unsigned long long edges_seen; // running sum of out_edges over processed frontiers
-    unsigned pad3[20];
+    unsigned long long round_t[4];   // CTA 0's clock at the start of round r (entry r % 4)
+    unsigned long long exp_edges[4]; // edges expanded in round r (entry r % 4)
+    unsigned exp_verts[4];           // vertices expanded in round r (entry r % 4)
+    unsigned dbg_site, dbg_value, dbg_round;  // PG_DEBUG_BOUNDS builds: first bad index
+    unsigned pad2[9];
     PgSlot slot[PG_NUM_SLOTS];
 };
 
@@ -86,40 +90,41 @@ __device__ __forceinline__ unsigned pg_lanemask_lt() {
     return m;
 }
 
-// Grid-wide barrier for a persistent, co-resident grid.  Every wait is
-// bounded: after `timeout_ns` (or an iteration cap) the waiter sets
-// PG_DEV_TIMEOUT and leaves; a waiter that sees the status already set
-// leaves at once.  Returns false when the traversal must stop.
-// The last arriver stamps Ctrl::t_release before opening the barrier.
+// Grid-wide barrier for a persistent, co-resident grid.  Thread 0 of every
+// CTA adds 1 to one monotone counter with release semantics and polls it
+// with relaxed loads until it reaches (generation + 1) * nblocks, then
+// fences (acquire).  Measured on GB300 at ~1.2 us for 152 CTAs, about half
+// a flag-array or arrive-and-flip barrier.  Every wait is bounded: after
+// `timeout_ns` (or an iteration cap) the waiter sets PG_DEV_TIMEOUT and
+// leaves; a waiter that sees the status set leaves at once.  Returns false
+// when the traversal must stop.
+__device__ __forceinline__ unsigned pg_ld_relaxed(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ bool pg_grid_sync(PgCtrl *c, unsigned nblocks, unsigned &gen,
                                              unsigned long long timeout_ns, int *s_flag) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned g = gen;
-        __threadfence();
-        const unsigned prev = atomicAdd(&c->bar_count, 1u);
-        if (prev == nblocks - 1) {
-            atomicExch(&c->bar_count, 0u);
-            *(volatile unsigned long long *)&c->t_release = pg_gtimer();
-            __threadfence();
-            pg_st_release(&c->bar_gen, g + 1);
-        } else {
-            const unsigned long long t0 = pg_gtimer();
-            unsigned long long it = 0;
-            while (pg_ld_acquire(&c->bar_gen) == g) {
-                if ((++it & 31ull) == 0) {
-                    if (pg_ld_volatile(&c->status) != 0u) break;
-                    if (pg_gtimer() - t0 > timeout_ns || it > (1ull << 34)) {
-                        atomicOr(&c->status, PG_DEV_TIMEOUT);
-                        break;
-                    }
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&c->bar_cnt) : "memory");
+        const unsigned target = (gen + 1u) * nblocks;
+        const unsigned long long t0 = pg_gtimer();
+        unsigned long long it = 0;
+        while ((int)(pg_ld_relaxed(&c->bar_cnt) - target) < 0) {
+            if ((++it & 31ull) == 0) {
+                if (pg_ld_volatile(&c->status) != 0u) break;
+                if (pg_gtimer() - t0 > timeout_ns || it > (1ull << 34)) {
+                    atomicOr(&c->status, PG_DEV_TIMEOUT);
+                    break;
                 }
             }
         }
-        __threadfence();
-        gen = g + 1;
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
         *s_flag = (pg_ld_volatile(&c->status) != 0u);
     }
+    gen++;
     __syncthreads();
     return *s_flag == 0;
 }
@@ -150,6 +155,9 @@ struct pg_graph {
     uint32_t n, m, flags;
     bool has_transpose, transpose_is_self;
     uint32_t *d_off, *d_idx, *d_toff, *d_tidx;
+    uint32_t *d_ell[2];   // padded adjacency rows (forward, reverse) or null
+    uint32_t ellw[2];     // their width: 4, 8 or 16 neighbour slots, 0 = none
+    uint32_t maxdeg[2];   // largest out-degree (forward, reverse)
     // traversal workspace
     uint32_t *d_bag;      // 2 * bag_cap
     uint32_t bag_cap;
@@ -170,6 +178,7 @@ struct pg_graph {
     bool has_weights;
     PgMsbfsWork *msbfs;
     int num_sms;
+    cudaEvent_t ev0, ev1;  // bracket the traversal kernel of the last call
 };
 
 // per-call launch parameters resolved from pg_config

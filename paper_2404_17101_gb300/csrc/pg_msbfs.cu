@@ -163,7 +163,8 @@ __global__ void __launch_bounds__(512) pg_msbfs_kernel(const MsArgs A) {
 #pragma unroll
                     for (uint32_t step = 16; step >= 1; step >>= 1)
                         if (s_incl[wib][o + step - 1] <= j) o += step;
-                    const uint32_t w = __ldg(A.G.idx + s_base[wib][o] + j);
+                    const uint32_t e = s_base[wib][o] + j;  // u32 sum (the base may wrap)
+                    const uint32_t w = __ldg(A.G.idx + e);
                     atomicOr(A.next + w, s_bits[wib][o]);
                 }
                 __syncwarp();
@@ -267,7 +268,9 @@ pg_status pg_launch_msbfs(pg_graph *g, PgLaunch &L, const uint32_t *sources, uin
     L.threads = threads;
     PG_CK(cudaMemsetAsync(g->d_ctrl, 0, sizeof(PgCtrl), s));
     void *args[] = {(void *)&A};
+    PG_CK(cudaEventRecord(g->ev0, s));
     PG_CK(cudaLaunchCooperativeKernel((const void *)pg_msbfs_kernel, dim3(bps * g->num_sms),
                                       dim3(threads), args, 0, s));
+    PG_CK(cudaEventRecord(g->ev1, s));
     return PG_OK;
 }

@@ -5,32 +5,47 @@
 //   BFS   (Sec. 2.2): value = uint32 hop distance, relax = atomicMin(d + 1);
 //   REACH (Sec. 2.1): value = uint64 source bitmask, relax = atomicOr(mask),
 //                     forward (G) and backward (G^T) searches share the rounds.
-// Vertical granularity control (Sec. 2.1) is a per-warp local search: a warp
-// that takes a chunk of c frontier entries may expand up to c*(tau-1)
-// further vertices it improves, held in a shared-memory FIFO, before new
-// improvements spill to the next frontier bag.  Any vertex whose value
-// improves is expanded again later (label-correcting, Sec. 2.2), so the
-// result is the exact fixpoint for every tau and every push/pull sequence.
 //
-// Frontier bags (the paper's hash bag, Sec. 2.1 "Data Structure Design",
-// rethought for the GPU): a flat array per round parity with a global tail
-// and warp-aggregated appends, de-duplicated by a per-vertex round tag.
-// Vertices of out-degree >= hub_degree are also listed as hubs when
-// appended; their edges are split into fixed chunks taken by any warp.
+// Vertical granularity control (Sec. 2.1) on the GPU is a per-warp tau-hop
+// local search: a warp takes a chunk of frontier entries and keeps expanding
+// the vertices it improves, from a shared-memory FIFO, as long as they lie
+// within tau hops of the round's frontier (BFS: new distance < L + tau,
+// L = smallest distance in the frontier; REACH: hop count < tau) and a
+// per-task budget lasts; other improvements spill to the next frontier bag.
+// A vertex whose value improves is always expanded again later (Sec. 2.2:
+// a vertex can be visited multiple times), so the result is the exact
+// fixpoint for every tau and every push/pull sequence.
+//
+// Frontier bags (the hash bag of Sec. 2.1, rethought): a flat array per
+// round parity with a global tail; spills are staged per warp in shared
+// memory and appended 128 at a time with one atomicAdd, de-duplicated by a
+// per-vertex round tag (skipped in level-pure plain rounds, where every
+// vertex can only improve once).
+// Neighbour lists come from padded rows (4/8/16 ids per vertex, one to four
+// 16-byte loads, no offsets lookup) when the graph's degrees are low, else
+// from the CSR with a warp-cooperative edge deal.  Vertices of out-degree
+// >= hub_degree are listed as hubs when appended and their edges are split
+// into fixed chunks that any warp takes.
 // Pull rounds (direction optimisation [Beamer12], Sec. 2.2) run at the
-// settled level L = smallest tentative distance among active vertices.
+// settled level L, the smallest tentative distance among active vertices:
+// every vertex with true distance <= L already holds it, so a bottom-up
+// sweep at L yields exactly level L + 1.
 #include <cstdio>
 
 #include "pg_internal.cuh"
 
 namespace {
 
-constexpr int kU = 4;                 // 32-edge batches in flight per step
+constexpr int kU = 4;                   // 32-wide batches in flight per step
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr unsigned long long kMask40 = (1ull << 40) - 1;
+constexpr uint32_t kSpillCap = 32u * kU;  // per-warp spill staging entries
+constexpr uint32_t kMaxW = 16;            // widest padded row
 
 struct TravArgs {
     PgGraphDev G;
+    const uint32_t *ell0, *ell1;  // padded rows (forward, reverse) or null
+    uint32_t ellw0, ellw1;        // their widths
     PgCtrl *ctrl;
     uint32_t *bag;        // [2][cap]
     uint32_t cap;
@@ -38,19 +53,44 @@ struct TravArgs {
     PgHub *hubs;          // [2][hcap]
     uint32_t hcap;
     uint32_t *dist;       // BFS output
-    unsigned long long *mask[2];  // REACH outputs (fwd, bwd)
+    unsigned long long *mask0, *mask1;  // REACH outputs (forward, backward)
     uint32_t src;
     uint32_t k, dir;
+    uint32_t need_deg;       // exact out-degree sums at append time (Beamer test)
+    uint32_t hubs_possible;  // some out-degree >= hub_degree
     uint32_t sources[64];
     PgLaunch L;
 };
 
+// Self-checking builds (-DPG_DEBUG_BOUNDS): every vertex id that enters a
+// wave (bag entry, local-queue entry, padded-row slot, CSR index) is checked
+// against n; the first bad one is recorded in the control block with its
+// site code and the id is replaced by "no vertex", so nothing out of range
+// is ever dereferenced.
+#ifdef PG_DEBUG_BOUNDS
+__device__ __forceinline__ uint32_t dbg_id(const TravArgs &A, uint32_t ent, uint32_t site, bool is_entry,
+                                          bool reach) {
+    if (ent == PG_NONE) return ent;
+    const uint32_t v = reach ? (ent & 0x7FFFFFFFu) : ent;
+    if (v < A.G.n) return ent;
+    if (atomicCAS(&A.ctrl->dbg_site, 0u, site) == 0u) {
+        A.ctrl->dbg_value = ent;
+        A.ctrl->dbg_round = A.ctrl->rounds;
+    }
+    return is_entry ? PG_NONE : PG_NONE;
+}
+#define PG_DBG_ENTRY(A, e, site, reach) dbg_id(A, e, site, true, reach)
+#define PG_DBG_ID(A, e, site, reach) dbg_id(A, e, site, false, reach)
+#else
+#define PG_DBG_ENTRY(A, e, site, reach) (e)
+#define PG_DBG_ID(A, e, site, reach) (e)
+#endif
+
 struct WarpSm {
-    uint32_t *lq;            // local queue [qcap]
-    uint32_t *s_incl;        // [32] inclusive degree prefix of the wave
-    uint32_t *s_base;        // [32] row start - exclusive prefix
-    uint32_t *s_dir;         // [32] direction of the owner (REACH)
-    unsigned long long *s_val;  // [32] value to propagate (BFS: d + 1)
+    uint32_t *lq, *lqa;      // local FIFO [qcap]: entry, aux (BFS: distance, REACH: hops)
+    uint32_t *sp, *spa;      // spill staging [kSpillCap]: entry, aux
+    uint32_t *s_incl, *s_base, *s_dir, *s_aux;  // [32] CSR wave bookkeeping
+    unsigned long long *s_val;                  // [32]
 };
 
 struct Round {
@@ -59,10 +99,20 @@ struct Round {
     uint32_t tag;            // round tag of the bag being filled
     uint32_t tau;
     uint32_t F;
+    uint32_t Lbase;          // smallest distance pushed into the bag read
+    bool dedupe;             // false only in level-pure plain push rounds
+    unsigned long long hub_pack;
+};
+
+struct Task {
+    uint32_t qhead, qtail;   // local FIFO cursors (warp-uniform)
+    uint32_t budget;         // local enqueues left
+    uint32_t nsp;            // staged spills
 };
 
 struct Counters {
-    unsigned long long expansions = 0, pushes = 0;
+    unsigned long long expansions = 0, pushes = 0, exp_edges = 0;
+    unsigned exp_verts = 0;
 };
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
@@ -86,6 +136,12 @@ __device__ __forceinline__ uint32_t warp_min(uint32_t x) {
     return x;
 }
 
+__device__ __forceinline__ uint32_t warp_max(uint32_t x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(kFull, x, o));
+    return x;
+}
+
 template <bool kReach>
 __device__ __forceinline__ const uint32_t *row_off(const TravArgs &A, uint32_t dir) {
     return (kReach && dir) ? A.G.toff : A.G.off;
@@ -95,33 +151,43 @@ __device__ __forceinline__ const uint32_t *row_idx(const TravArgs &A, uint32_t d
     return (kReach && dir) ? A.G.tidx : A.G.idx;
 }
 
-// Append the lanes' improved vertices (go[u]) to the next bag.  Warp-
+// Append up to kU*32 entries (lane-major batches) to the next bag.  Warp-
 // collective: every lane calls it with the same control flow.
-//   - de-duplication: atomicExch of the round tag into stamp[key]
-//   - one atomicAdd on the bag tail per warp call
-//   - out-degree sum for the schedule statistics, hub registration
-//   - BFS: min tentative distance over all attempted pushes (kept even when
-//     the push was de-duplicated), which defines the settled level.
+//   - de-duplication: atomicExch of the round tag into stamp[key] (skipped
+//     when the round cannot produce duplicates)
+//   - one atomicAdd on the bag tail per call
+//   - out-degree sum (schedule statistics) and hub registration when needed
+//   - BFS: min / max distance over all attempted appends (kept even when the
+//     append was de-duplicated); the min defines the settled level.
 template <bool kReach>
-__device__ void push_global(const TravArgs &A, const Round &R, const uint32_t (&w)[kU],
-                            const uint32_t (&dirv)[kU], const uint32_t (&nd)[kU],
-                            const bool (&go)[kU], int lane, Counters &C) {
+__device__ void push_global(const TravArgs &A, const Round &R, const uint32_t (&ent)[kU],
+                            const uint32_t (&nd)[kU], const bool (&go)[kU], int lane,
+                            Counters &C) {
     bool keep[kU];
     uint32_t deg[kU];
+    const bool want_deg = A.need_deg || A.hubs_possible;
 #pragma unroll
     for (int u = 0; u < kU; u++) {
         keep[u] = false;
         deg[u] = 0;
         if (go[u]) {
-            const uint32_t key = w[u] + ((kReach && dirv[u]) ? A.G.n : 0u);
-            keep[u] = atomicExch(&A.stamp[key], R.tag) != R.tag;
+            if (R.dedupe) {
+                const uint32_t w = kReach ? (ent[u] & 0x7FFFFFFFu) : ent[u];
+                const uint32_t key = w + ((kReach && (ent[u] >> 31)) ? A.G.n : 0u);
+                keep[u] = atomicExch(&A.stamp[key], R.tag) != R.tag;
+            } else {
+                keep[u] = true;
+            }
         }
     }
+    if (want_deg) {
 #pragma unroll
-    for (int u = 0; u < kU; u++) {
-        if (go[u]) {
-            const uint32_t *o = row_off<kReach>(A, dirv[u]);
-            deg[u] = __ldg(o + w[u] + 1) - __ldg(o + w[u]);
+        for (int u = 0; u < kU; u++) {
+            if (go[u]) {
+                const uint32_t w = kReach ? (ent[u] & 0x7FFFFFFFu) : ent[u];
+                const uint32_t *o = row_off<kReach>(A, kReach ? (ent[u] >> 31) : 0u);
+                deg[u] = __ldg(o + w + 1) - __ldg(o + w);
+            }
         }
     }
     unsigned bal[kU];
@@ -134,12 +200,16 @@ __device__ void push_global(const TravArgs &A, const Round &R, const uint32_t (&
         total += __popc(bal[u]);
     }
     if (!kReach) {
-        uint32_t mn = PG_INF;
+        uint32_t mn = PG_INF, mx = 0;
 #pragma unroll
         for (int u = 0; u < kU; u++)
-            if (go[u]) mn = min(mn, nd[u]);
+            if (go[u]) { mn = min(mn, nd[u]); mx = max(mx, nd[u]); }
         mn = warp_min(mn);
-        if (lane == 0 && mn != PG_INF) atomicMin(&R.sn->min_level, mn);
+        mx = warp_max(mx);
+        if (lane == 0 && mn != PG_INF) {
+            atomicMin(&R.sn->min_level, mn);
+            atomicMax(&R.sn->max_level, mx);
+        }
     }
     if (total == 0) return;
     uint32_t pos = 0;
@@ -151,20 +221,19 @@ __device__ void push_global(const TravArgs &A, const Round &R, const uint32_t (&
     for (int u = 0; u < kU; u++) {
         if (keep[u]) {
             const uint32_t p = pos + before[u] + __popc(bal[u] & lt);
-            const uint32_t entry = kReach ? (w[u] | (dirv[u] << 31)) : w[u];
             if (p < A.cap) {
-                A.bag[(size_t)R.nxt * A.cap + p] = entry;
+                A.bag[(size_t)R.nxt * A.cap + p] = ent[u];
             } else {
                 atomicOr(&A.ctrl->status, PG_DEV_OVERFLOW);
             }
             dsum += deg[u];
-            if (deg[u] >= A.L.hub_degree) {
+            if (A.hubs_possible && deg[u] >= A.L.hub_degree) {
                 const unsigned long long pk =
                     atomicAdd(&R.sn->hub_pack, (1ull << 40) | (unsigned long long)deg[u]);
                 const uint32_t hi = (uint32_t)(pk >> 40);
                 if (hi < A.hcap) {
                     PgHub h;
-                    h.v = entry;
+                    h.v = ent[u];
                     h.start = (uint32_t)(pk & kMask40);
                     A.hubs[(size_t)R.nxt * A.hcap + hi] = h;
                 } else {
@@ -173,129 +242,216 @@ __device__ void push_global(const TravArgs &A, const Round &R, const uint32_t (&
             }
         }
     }
-    dsum = warp_sum64(dsum);
-    if (lane == 0) atomicAdd(&R.sn->out_edges, dsum);
+    if (want_deg) {
+        dsum = warp_sum64(dsum);
+        if (lane == 0 && dsum) atomicAdd(&R.sn->out_edges, dsum);
+    }
     C.pushes += (lane == 0) ? total : 0;
 }
 
-// Value a vertex propagates: BFS d+1 (INF stays INF), REACH its mask.
+// Append every staged spill of this warp to the next bag.
+template <bool kReach>
+__device__ void flush_spill(const TravArgs &A, const Round &R, const WarpSm &S, Task &T, int lane,
+                            Counters &C) {
+    __syncwarp();
+    for (uint32_t base = 0; base < T.nsp; base += kSpillCap) {
+        uint32_t ent[kU], nd[kU];
+        bool go[kU];
+#pragma unroll
+        for (int u = 0; u < kU; u++) {
+            const uint32_t i = base + (uint32_t)u * 32u + (uint32_t)lane;
+            go[u] = i < T.nsp;
+            ent[u] = go[u] ? S.sp[i] : 0u;
+            nd[u] = go[u] ? S.spa[i] : 0u;
+        }
+        push_global<kReach>(A, R, ent, nd, go, lane, C);
+    }
+    T.nsp = 0;
+    __syncwarp();
+}
+
+// Route one improved entry per lane: into the local FIFO if it is eligible
+// and there is room and budget, else into the spill staging.
+template <bool kReach>
+__device__ __forceinline__ void stage(const TravArgs &A, const Round &R, const WarpSm &S, Task &T,
+                                      bool imp, uint32_t ent, uint32_t aux, bool eligible,
+                                      int lane, Counters &C) {
+    const unsigned lt = pg_lanemask_lt();
+    const bool want = imp && eligible;
+    const unsigned bl = __ballot_sync(kFull, want);
+    bool to_local = false;
+    if (bl) {
+        const uint32_t room = min(A.L.qcap - (T.qtail - T.qhead), T.budget);
+        const uint32_t nl = min((uint32_t)__popc(bl), room);
+        const uint32_t rank = __popc(bl & lt);
+        to_local = want && rank < nl;
+        if (to_local) {
+            const uint32_t p = (T.qtail + rank) & (A.L.qcap - 1);
+            S.lq[p] = ent;
+            S.lqa[p] = aux;
+        }
+        T.qtail += nl;
+        T.budget -= nl;
+    }
+    const bool to_spill = imp && !to_local;
+    const unsigned bs = __ballot_sync(kFull, to_spill);
+    if (bs) {
+        if (T.nsp + (uint32_t)__popc(bs) > kSpillCap) flush_spill<kReach>(A, R, S, T, lane, C);
+        if (to_spill) {
+            const uint32_t p = T.nsp + __popc(bs & lt);
+            S.sp[p] = ent;
+            S.spa[p] = aux;
+        }
+        T.nsp += __popc(bs);
+    }
+}
+
+// Value a vertex propagates: BFS d + 1 (INF stays INF), REACH its mask.
 template <bool kReach>
 __device__ __forceinline__ unsigned long long load_prop(const TravArgs &A, uint32_t v,
                                                         uint32_t dir) {
-    if (kReach) return pg_ldcg64(A.mask[dir] + v);
+    if (kReach) return pg_ldcg64((dir ? A.mask1 : A.mask0) + v);
     const uint32_t d = pg_ldcg(A.dist + v);
     return d == PG_INF ? (unsigned long long)PG_INF : (unsigned long long)(d + 1);
 }
 
-// Relax arc (.., w) with propagated value p; returns true if w improved.
+// Relax arc (.., w) with propagated value p; true if w improved.
 template <bool kReach>
 __device__ __forceinline__ bool relax(const TravArgs &A, uint32_t w, uint32_t dir,
-                                      unsigned long long p) {
+                                     unsigned long long p) {
     if (kReach) {
-        const unsigned long long old = atomicOr(A.mask[dir] + w, p);
+        const unsigned long long old = atomicOr((dir ? A.mask1 : A.mask0) + w, p);
         return (p & ~old) != 0ull;
     }
     const uint32_t nd = (uint32_t)p;
     return nd < atomicMin(A.dist + w, nd);
 }
 
-// Expand one wave (<= 32 vertices, one per lane) cooperatively: the wave's
-// out-edges are laid end to end and dealt 32 per step to the lanes, with
-// kU steps in flight.  Improved vertices go to the warp's local queue while
-// the VGC budget and queue space last, otherwise to the next bag.
+// Local eligibility of a child with aux value `caux` (BFS: its distance,
+// REACH: its hop count).
 template <bool kReach>
-__device__ void expand_wave(const TravArgs &A, const Round &R, const WarpSm &S, uint32_t entry,
-                            bool from_bag, uint32_t &budget, uint32_t &qhead, uint32_t &qtail,
-                            int lane, Counters &C) {
-    const uint32_t qmask = A.L.qcap - 1;
+__device__ __forceinline__ bool eligible(const Round &R, uint32_t caux) {
+    return kReach ? (caux < R.tau) : (caux < R.Lbase + R.tau);
+}
+
+// Expand one wave (<= 32 vertices, one per lane).
+template <bool kReach>
+__device__ void expand_wave(const TravArgs &A, const Round &R, const WarpSm &S, Task &T,
+                            uint32_t entry, uint32_t aux, bool from_bag, int lane, Counters &C) {
     uint32_t v = PG_NONE, dir = 0;
-    if (entry != PG_NONE) {
+    const bool valid = entry != PG_NONE;
+    if (valid) {
         v = kReach ? (entry & 0x7FFFFFFFu) : entry;
         dir = kReach ? (entry >> 31) : 0u;
     }
+    const uint32_t *ell = dir ? A.ell1 : A.ell0;
+    const uint32_t W = dir ? A.ellw1 : A.ellw0;
+    // fetch: value and padded row in parallel
     unsigned long long prop = 0;
+    uint32_t row[kMaxW];
+#pragma unroll
+    for (int j = 0; j < (int)kMaxW; j++) row[j] = PG_NONE;
+    bool use_row = false;
+    if (valid) {
+        prop = load_prop<kReach>(A, v, dir);
+        if (ell != nullptr) {
+            use_row = true;
+            const uint4 *rp = reinterpret_cast<const uint4 *>(ell + (size_t)v * W);
+#pragma unroll
+            for (int q = 0; q < (int)(kMaxW / 4); q++) {
+                if ((uint32_t)q * 4u < W) {
+                    const uint4 t = __ldg(rp + q);
+                    row[4 * q] = t.x; row[4 * q + 1] = t.y; row[4 * q + 2] = t.z; row[4 * q + 3] = t.w;
+                }
+            }
+#ifdef PG_DEBUG_BOUNDS
+            for (int j = 0; j < (int)kMaxW; j++)
+                if (row[j] < 0x80000000u) row[j] = PG_DBG_ID(A, row[j], 3u, false);
+#endif
+        }
+    }
+    const bool dead = !kReach && prop == (unsigned long long)PG_INF;
+    const bool is_long = valid && !dead && (!use_row || row[0] == PG_ELL_LONG);
+    // CSR row for long lanes (dependent load, rare when padded rows exist)
     uint32_t beg = 0, deg = 0;
     bool hub_repush = false;
-    if (v != PG_NONE) {
+    if (is_long) {
         const uint32_t *o = row_off<kReach>(A, dir);
         beg = __ldg(o + v);
         deg = __ldg(o + v + 1) - beg;
-        prop = load_prop<kReach>(A, v, dir);
-        if (deg >= A.L.hub_degree) {
-            // hubs from the bag are expanded through the hub list; a hub met
-            // by a local search is sent to the next bag (listed there)
-            hub_repush = !from_bag;
+        if (A.hubs_possible && deg >= A.L.hub_degree) {
+            hub_repush = !from_bag;  // a hub met by a local search goes to the next bag
             deg = 0;
-        } else if (!kReach && prop == (unsigned long long)PG_INF) {
-            deg = 0;
-        } else {
-            C.expansions++;
         }
     }
-    {
-        const bool any = __any_sync(kFull, hub_repush);
-        if (any) {
-            uint32_t w1[kU] = {v, 0, 0, 0}, d1[kU] = {dir, 0, 0, 0};
-            uint32_t n1[kU] = {(uint32_t)(prop - 1), 0, 0, 0};
-            bool g1[kU] = {hub_repush, false, false, false};
-            push_global<kReach>(A, R, w1, d1, n1, g1, lane, C);
+    const uint32_t caux = kReach ? aux + 1u : (uint32_t)prop;
+    const bool ok_local = eligible<kReach>(R, caux);
+    // padded rows: relax every slot (all atomics in flight), then stage
+    const bool row_lane = use_row && valid && !dead && !is_long;
+    if (__any_sync(kFull, row_lane)) {
+        bool imp[kMaxW];
+        uint32_t nvalid = 0;
+#pragma unroll
+        for (int j = 0; j < (int)kMaxW; j++) {
+            const bool ok = row_lane && (uint32_t)j < W && row[j] < 0x80000000u;
+            nvalid += ok ? 1u : 0u;
+            imp[j] = ok && relax<kReach>(A, row[j], dir, prop);
+        }
+        if (row_lane) { C.expansions++; C.exp_verts++; C.exp_edges += nvalid; }
+        const uint32_t wmax = max(A.ellw0, A.ellw1);
+#pragma unroll
+        for (int j = 0; j < (int)kMaxW; j++) {
+            if ((uint32_t)j < wmax)
+                stage<kReach>(A, R, S, T, imp[j], kReach ? (row[j] | (dir << 31)) : row[j],
+                              caux, ok_local, lane, C);
         }
     }
+    if (__any_sync(kFull, hub_repush))
+        stage<kReach>(A, R, S, T, hub_repush, entry, kReach ? aux : (uint32_t)(prop - 1), false,
+                      lane, C);
+    // CSR rows: the wave's edges laid end to end, dealt 32 per step
     const uint32_t incl = warp_incl_scan(deg, lane);
     const uint32_t total = __shfl_sync(kFull, incl, 31);
     if (total == 0) return;
+    if (deg) { C.expansions++; C.exp_verts++; C.exp_edges += deg; }
+    __syncwarp();
     S.s_incl[lane] = incl;
     S.s_base[lane] = beg - (incl - deg);
     S.s_val[lane] = prop;
     S.s_dir[lane] = dir;
+    S.s_aux[lane] = caux;
     __syncwarp();
-    const unsigned lt = pg_lanemask_lt();
     for (uint32_t base = 0; base < total; base += 32u * kU) {
-        uint32_t w[kU], wd[kU], nd[kU];
+        uint32_t w[kU], wd[kU], ca[kU];
         unsigned long long pv[kU];
-        bool ok[kU], imp[kU], go[kU];
+        bool ok[kU], imp[kU];
 #pragma unroll
         for (int u = 0; u < kU; u++) {
             const uint32_t j = base + (uint32_t)u * 32u + (uint32_t)lane;
             ok[u] = j < total;
-            w[u] = 0; wd[u] = 0; pv[u] = 0;
+            w[u] = 0; wd[u] = 0; pv[u] = 0; ca[u] = 0;
             if (ok[u]) {
                 uint32_t o = 0;
 #pragma unroll
                 for (uint32_t step = 16; step >= 1; step >>= 1)
                     if (S.s_incl[o + step - 1] <= j) o += step;
-                const uint32_t e = S.s_base[o] + j;
                 wd[u] = S.s_dir[o];
                 pv[u] = S.s_val[o];
+                ca[u] = S.s_aux[o];
+                // u32 sum first: s_base = row start - prefix may wrap
+                const uint32_t e = S.s_base[o] + j;
                 w[u] = __ldg(row_idx<kReach>(A, wd[u]) + e);
+#ifdef PG_DEBUG_BOUNDS
+                if (PG_DBG_ID(A, w[u], 4u, false) == PG_NONE) { ok[u] = false; w[u] = 0; }
+#endif
             }
         }
 #pragma unroll
-        for (int u = 0; u < kU; u++) {
-            imp[u] = ok[u] && relax<kReach>(A, w[u], wd[u], pv[u]);
-            nd[u] = (uint32_t)pv[u];
-        }
+        for (int u = 0; u < kU; u++) imp[u] = ok[u] && relax<kReach>(A, w[u], wd[u], pv[u]);
 #pragma unroll
-        for (int u = 0; u < kU; u++) {
-            const unsigned b = __ballot_sync(kFull, imp[u]);
-            go[u] = false;
-            if (b) {
-                const uint32_t cnt = __popc(b);
-                const uint32_t rank = __popc(b & lt);
-                const uint32_t space = min(A.L.qcap - (qtail - qhead), budget);
-                const uint32_t nloc = min(cnt, space);
-                if (imp[u]) {
-                    if (rank < nloc) {
-                        S.lq[(qtail + rank) & qmask] = kReach ? (w[u] | (wd[u] << 31)) : w[u];
-                    } else {
-                        go[u] = true;
-                    }
-                }
-                qtail += nloc;
-                budget -= nloc;
-            }
-        }
-        push_global<kReach>(A, R, w, wd, nd, go, lane, C);
+        for (int u = 0; u < kU; u++)
+            stage<kReach>(A, R, S, T, imp[u], kReach ? (w[u] | (wd[u] << 31)) : w[u], ca[u],
+                          eligible<kReach>(R, ca[u]), lane, C);
     }
     __syncwarp();
 }
@@ -304,32 +460,44 @@ __device__ void expand_wave(const TravArgs &A, const Round &R, const WarpSm &S, 
 template <bool kReach>
 __device__ void run_task(const TravArgs &A, const Round &R, const WarpSm &S, uint32_t entry,
                          uint32_t c, int lane, Counters &C) {
-    uint32_t budget = c * (R.tau - 1u);
-    uint32_t qhead = 0, qtail = 0;
+    Task T;
+    T.qhead = T.qtail = 0;
+    T.nsp = 0;
+    T.budget = (R.tau > 1u) ? c * R.tau * 8u : 0u;
+    uint32_t aux = 0;
     bool from_bag = true;
     for (;;) {
-        expand_wave<kReach>(A, R, S, entry, from_bag, budget, qhead, qtail, lane, C);
-        const uint32_t avail = qtail - qhead;
+        expand_wave<kReach>(A, R, S, T, entry, aux, from_bag, lane, C);
+        const uint32_t avail = T.qtail - T.qhead;
         if (avail == 0) break;
         const uint32_t take = min(32u, avail);
         __syncwarp();
-        entry = ((uint32_t)lane < take) ? S.lq[(qhead + lane) & (A.L.qcap - 1)] : PG_NONE;
-        qhead += take;
+        const uint32_t p = (T.qhead + lane) & (A.L.qcap - 1);
+        entry = ((uint32_t)lane < take) ? S.lq[p] : PG_NONE;
+        entry = PG_DBG_ENTRY(A, entry, 2u, kReach);
+        aux = ((uint32_t)lane < take) ? S.lqa[p] : 0u;
+        T.qhead += take;
         from_bag = false;
         __syncwarp();
     }
+    flush_spill<kReach>(A, R, S, T, lane, C);
 }
 
 // Edges of listed hubs, dealt in chunks of `hch` edges (hch <= hub_degree, so
-// a chunk touches at most two hubs).  Improvements go straight to the bag.
+// a chunk touches at most two hubs).  Improvements go to the next bag.
 template <bool kReach>
-__device__ void hub_edges(const TravArgs &A, const Round &R, int lane, Counters &C) {
-    const unsigned long long hp = pg_ldcg64(&R.sc->hub_pack);
+__device__ void hub_edges(const TravArgs &A, const Round &R, const WarpSm &S, int lane,
+                          Counters &C) {
+    const unsigned long long hp = R.hub_pack;
     const uint32_t hcount = min((uint32_t)(hp >> 40), A.hcap);
     const uint32_t hedges = (uint32_t)(hp & kMask40);
     if (hcount == 0) return;
     const uint32_t hch = min(1024u, A.L.hub_degree);
     const PgHub *H = A.hubs + (size_t)R.cur * A.hcap;
+    Task T;
+    T.qhead = T.qtail = 0;
+    T.nsp = 0;
+    T.budget = 0;
     for (;;) {
         uint32_t a = 0;
         if (lane == 0) a = atomicAdd(&R.sc->hub_cursor, hch);
@@ -341,24 +509,24 @@ __device__ void hub_edges(const TravArgs &A, const Round &R, int lane, Counters 
             const uint32_t mid = (lo + hi) >> 1;
             if (__ldcg(&H[mid].start) <= a) lo = mid; else hi = mid;
         }
-        uint32_t hv[2], hs[2], hb[2], hd[2], hdeg[2];
+        uint32_t hs[2], hb[2], hd[2], hdeg[2];
         unsigned long long hpv[2];
         for (int t = 0; t < 2; t++) {
-            hs[t] = PG_INF; hv[t] = 0; hb[t] = 0; hd[t] = 0; hpv[t] = 0; hdeg[t] = 0;
+            hs[t] = PG_INF; hb[t] = 0; hd[t] = 0; hpv[t] = 0; hdeg[t] = 0;
             const uint32_t i = lo + t;
             if (i < hcount) {
                 const uint32_t e = __ldcg(&H[i].v);
                 hs[t] = __ldcg(&H[i].start);
-                hv[t] = kReach ? (e & 0x7FFFFFFFu) : e;
+                const uint32_t hv = kReach ? (e & 0x7FFFFFFFu) : e;
                 hd[t] = kReach ? (e >> 31) : 0u;
-                hb[t] = __ldg(row_off<kReach>(A, hd[t]) + hv[t]);
-                hdeg[t] = __ldg(row_off<kReach>(A, hd[t]) + hv[t] + 1) - hb[t];
-                hpv[t] = load_prop<kReach>(A, hv[t], hd[t]);
+                hb[t] = __ldg(row_off<kReach>(A, hd[t]) + hv);
+                hdeg[t] = __ldg(row_off<kReach>(A, hd[t]) + hv + 1) - hb[t];
+                hpv[t] = load_prop<kReach>(A, hv, hd[t]);
             }
         }
         if (lane == 0) C.expansions += (hs[1] < a + len) ? 2 : 1;
         for (uint32_t t0 = 0; t0 < len; t0 += 32u * kU) {
-            uint32_t w[kU], wd[kU], nd[kU];
+            uint32_t w[kU], wd[kU];
             unsigned long long pv[kU];
             bool go[kU];
 #pragma unroll
@@ -374,43 +542,74 @@ __device__ void hub_edges(const TravArgs &A, const Round &R, int lane, Counters 
                         pv[u] = hpv[t];
                         w[u] = __ldg(row_idx<kReach>(A, hd[t]) + hb[t] + rel);
                         go[u] = !(!kReach && pv[u] == (unsigned long long)PG_INF);
+#ifdef PG_DEBUG_BOUNDS
+                        if (PG_DBG_ID(A, w[u], 5u, false) == PG_NONE) { go[u] = false; w[u] = 0; }
+#endif
                     }
                 }
             }
 #pragma unroll
-            for (int u = 0; u < kU; u++) {
-                go[u] = go[u] && relax<kReach>(A, w[u], wd[u], pv[u]);
-                nd[u] = (uint32_t)pv[u];
-            }
-            push_global<kReach>(A, R, w, wd, nd, go, lane, C);
+            for (int u = 0; u < kU; u++) go[u] = go[u] && relax<kReach>(A, w[u], wd[u], pv[u]);
+#pragma unroll
+            for (int u = 0; u < kU; u++)
+                stage<kReach>(A, R, S, T, go[u], kReach ? (w[u] | (wd[u] << 31)) : w[u],
+                              kReach ? 1u : (uint32_t)pv[u], false, lane, C);
         }
     }
+    flush_spill<kReach>(A, R, S, T, lane, C);
 }
 
 // Bottom-up round at settled level L (BFS only): every vertex with
-// dist > L+1 looks for an in-neighbour at distance L (first match wins) and
-// takes L+1; bag entries still above L stay active.
-__device__ void pull_round(const TravArgs &A, const Round &R, uint32_t Lvl, int lane,
-                           uint32_t gwarp, uint32_t nwarps, Counters &C) {
+// dist > L + 1 looks for an in-neighbour at distance L and takes L + 1;
+// bag entries still above L stay active.
+__device__ void pull_round(const TravArgs &A, const Round &R, const WarpSm &S, uint32_t Lvl,
+                           int lane, uint32_t gwarp, uint32_t nwarps, Counters &C) {
     const uint32_t n = A.G.n;
     const uint32_t target = Lvl + 1u;
+    Task T;
+    T.qhead = T.qtail = 0;
+    T.nsp = 0;
+    T.budget = 0;
+    const uint32_t W = A.ellw1;
     for (uint32_t base = gwarp * 32u; base < n; base += nwarps * 32u) {
         const uint32_t v = base + lane;
         bool found = false;
         if (v < n) {
             const uint32_t d = pg_ldcg(A.dist + v);
             if (d > target) {
-                const uint32_t b = __ldg(A.G.toff + v), e = __ldg(A.G.toff + v + 1);
-                for (uint32_t q = b; q < e; q++) {
-                    const uint32_t u = __ldg(A.G.tidx + q);
-                    if (pg_ldcg(A.dist + u) == Lvl) { found = true; break; }
+                bool use_csr = true;
+                if (A.ell1 != nullptr) {
+                    const uint4 *rp = reinterpret_cast<const uint4 *>(A.ell1 + (size_t)v * W);
+                    uint32_t row[kMaxW];
+#pragma unroll
+                    for (int j = 0; j < (int)kMaxW; j++) row[j] = PG_NONE;
+#pragma unroll
+                    for (int q = 0; q < (int)(kMaxW / 4); q++) {
+                        if ((uint32_t)q * 4u < W) {
+                            const uint4 t = __ldg(rp + q);
+                            row[4 * q] = t.x; row[4 * q + 1] = t.y; row[4 * q + 2] = t.z;
+                            row[4 * q + 3] = t.w;
+                        }
+                    }
+                    if (row[0] != PG_ELL_LONG) {
+                        use_csr = false;
+#pragma unroll
+                        for (int j = 0; j < (int)kMaxW; j++)
+                            if ((uint32_t)j < W && row[j] < 0x80000000u &&
+                                pg_ldcg(A.dist + row[j]) == Lvl)
+                                found = true;
+                    }
+                }
+                if (use_csr) {
+                    const uint32_t b = __ldg(A.G.toff + v), e = __ldg(A.G.toff + v + 1);
+                    for (uint32_t q = b; q < e; q++) {
+                        if (pg_ldcg(A.dist + __ldg(A.G.tidx + q)) == Lvl) { found = true; break; }
+                    }
                 }
                 if (found) A.dist[v] = target;
             }
         }
-        uint32_t w[kU] = {v, 0, 0, 0}, wd[kU] = {0, 0, 0, 0}, nd[kU] = {target, 0, 0, 0};
-        bool go[kU] = {found, false, false, false};
-        if (__any_sync(kFull, found)) push_global<false>(A, R, w, wd, nd, go, lane, C);
+        if (__any_sync(kFull, found)) stage<false>(A, R, S, T, found, v, target, false, lane, C);
     }
     for (uint32_t base = gwarp * 32u; base < R.F; base += nwarps * 32u) {
         const uint32_t i = base + lane;
@@ -418,13 +617,17 @@ __device__ void pull_round(const TravArgs &A, const Round &R, uint32_t Lvl, int 
         bool keep = false;
         if (i < R.F) {
             v = __ldcg(A.bag + (size_t)R.cur * A.cap + i);
-            d = pg_ldcg(A.dist + v);
-            keep = d > Lvl;
+            v = PG_DBG_ENTRY(A, v, 6u, false);
+            if (v != PG_NONE) {
+                d = pg_ldcg(A.dist + v);
+                keep = d > Lvl;
+            } else {
+                v = 0;
+            }
         }
-        uint32_t w[kU] = {v, 0, 0, 0}, wd[kU] = {0, 0, 0, 0}, nd[kU] = {d, 0, 0, 0};
-        bool go[kU] = {keep, false, false, false};
-        if (__any_sync(kFull, keep)) push_global<false>(A, R, w, wd, nd, go, lane, C);
+        if (__any_sync(kFull, keep)) stage<false>(A, R, S, T, keep, v, d, false, lane, C);
     }
+    flush_spill<false>(A, R, S, T, lane, C);
 }
 
 __device__ __forceinline__ void reset_slot(PgSlot *s) {
@@ -432,6 +635,7 @@ __device__ __forceinline__ void reset_slot(PgSlot *s) {
     s->head = 0;
     s->hub_cursor = 0;
     s->min_level = PG_INF;
+    s->max_level = 0;
     s->out_edges = 0;
     s->hub_pack = 0;
     s->settled = 0;
@@ -475,7 +679,7 @@ __device__ uint32_t mlp_decide(const float *W, const float (&x)[5], bool allow_p
 __device__ __forceinline__ float flog2p1(float x) { return log2f(1.0f + x); }
 
 template <bool kReach>
-__global__ void __launch_bounds__(512) pg_traverse_kernel(const TravArgs A) {
+__global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_flag;
     __shared__ uint32_t s_action;
@@ -486,17 +690,23 @@ __global__ void __launch_bounds__(512) pg_traverse_kernel(const TravArgs A) {
     const uint32_t nwarps = gridDim.x * nwib;
     const uint32_t nblocks = gridDim.x;
 
-    // shared memory carve-up
-    float *s_w = reinterpret_cast<float *>(smem);                       // 1512 floats
-    unsigned long long *s_val_all =
-        reinterpret_cast<unsigned long long *>(smem + 6144);            // [nwib][32]
+    // shared memory: MLP weights, then per warp: s_val[32] (u64), 4 x [32]
+    // u32 wave arrays, spill staging 2 x [kSpillCap], local FIFO 2 x [qcap]
+    float *s_w = reinterpret_cast<float *>(smem);
+    unsigned long long *s_val_all = reinterpret_cast<unsigned long long *>(smem + 6144);
     uint32_t *s_u32 = reinterpret_cast<uint32_t *>(smem + 6144 + nwib * 256);
+    const uint32_t per_warp = 4u * 32u + 2u * kSpillCap + 2u * A.L.qcap;
+    uint32_t *mine = s_u32 + (size_t)wib * per_warp;
     WarpSm S;
     S.s_val = s_val_all + wib * 32;
-    S.s_incl = s_u32 + wib * 96;
-    S.s_base = S.s_incl + 32;
-    S.s_dir = S.s_incl + 64;
-    S.lq = s_u32 + nwib * 96 + (size_t)wib * A.L.qcap;
+    S.s_incl = mine;
+    S.s_base = mine + 32;
+    S.s_dir = mine + 64;
+    S.s_aux = mine + 96;
+    S.sp = mine + 128;
+    S.spa = S.sp + kSpillCap;
+    S.lq = S.spa + kSpillCap;
+    S.lqa = S.lq + A.L.qcap;
 
     if (A.L.schedule == PG_SCHED_LEARNED)
         for (int i = threadIdx.x; i < (int)PG_MLP_NPARAMS; i += blockDim.x) s_w[i] = A.L.weights[i];
@@ -516,8 +726,8 @@ __global__ void __launch_bounds__(512) pg_traverse_kernel(const TravArgs A) {
             unsigned long long bits = 0;
             for (uint32_t j = 0; j < A.k; j++)
                 if (A.sources[j] == v) bits |= 1ull << j;
-            if (A.dir & PG_FWD) A.mask[0][v] = bits;
-            if (A.dir & PG_BWD) A.mask[1][v] = bits;
+            if (A.dir & PG_FWD) A.mask0[v] = bits;
+            if (A.dir & PG_BWD) A.mask1[v] = bits;
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -540,7 +750,7 @@ __global__ void __launch_bounds__(512) pg_traverse_kernel(const TravArgs A) {
                 const uint32_t entry = kReach ? (v | (d << 31)) : v;
                 A.bag[cnt++] = entry;
                 oe += dg;
-                if (dg >= A.L.hub_degree) {
+                if (A.hubs_possible && dg >= A.L.hub_degree) {
                     const unsigned long long pk = s0->hub_pack;
                     PgHub h;
                     h.v = entry;
@@ -552,21 +762,23 @@ __global__ void __launch_bounds__(512) pg_traverse_kernel(const TravArgs A) {
         }
         s0->size = cnt;
         s0->min_level = 0;
+        s0->max_level = 0;
         s0->out_edges = oe;
     }
     if (A.L.stall_block == blockIdx.x) return;  // fault injection: never arrive
     if (!pg_grid_sync(ctrl, nblocks, gen, tmo, &s_flag)) return;
 
     Counters C;
-    unsigned long long t_begin = __ldcg(&ctrl->t_release);
+    const unsigned long long t_start = pg_gtimer();
     // whole-launch limit: 16 x the per-wait limit, checked once per round
-    const unsigned long long t_deadline = t_begin + 16ull * tmo;
-    unsigned long long prev_ns = 0;
+    const unsigned long long t_deadline = t_start + 16ull * tmo;
+    const float avg_deg = (float)A.G.m / (float)max(n, 1u);
     unsigned long long edges_seen = 0;
     bool pull_state = false;
+    bool prev_plain = true;   // the initial bag is a single level
     uint32_t pull_rounds = 0;
     uint32_t r = 0;
-    bool ok = true;
+    unsigned long long t_round = 0;
     for (;; r++) {
         Round R;
         R.cur = r & 1u;
@@ -575,17 +787,29 @@ __global__ void __launch_bounds__(512) pg_traverse_kernel(const TravArgs A) {
         R.sn = &ctrl->slot[(r + 1) % PG_NUM_SLOTS];
         R.tag = A.L.epoch + r + 1u;
         R.F = __ldcg(&R.sc->size);
-        if (R.F == 0) break;
-        if ((A.L.max_rounds && r >= A.L.max_rounds) || R.tag == 0u) {
-            if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(&ctrl->status, PG_DEV_OVERFLOW);
-            break;
-        }
-        if (R.F > A.cap) {
-            if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(&ctrl->status, PG_DEV_OVERFLOW);
-            break;
-        }
-        const unsigned long long E = pg_ldcg64(&R.sc->out_edges);
+        const unsigned long long E_exact = pg_ldcg64(&R.sc->out_edges);
         const uint32_t Lvl = __ldcg(&R.sc->min_level);
+        const uint32_t Lmax = __ldcg(&R.sc->max_level);
+        R.hub_pack = pg_ldcg64(&R.sc->hub_pack);
+        R.Lbase = Lvl;
+        if (R.F == 0) break;
+        if ((A.L.max_rounds && r >= A.L.max_rounds) || R.tag == 0u || R.F > A.cap) {
+            if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(&ctrl->status, PG_DEV_OVERFLOW);
+            break;
+        }
+        // out-edges of F: exact when counted at append time, else F times the
+        // mean degree of the vertices expanded in the previous round
+        unsigned long long E = E_exact;
+        if (!A.need_deg && r > 0) {
+            const unsigned ev = __ldcg(&ctrl->exp_verts[(r - 1) & 3]);
+            const unsigned long long ee = pg_ldcg64(&ctrl->exp_edges[(r - 1) & 3]);
+            const float md = ev ? (float)ee / (float)ev : avg_deg;
+            E = (unsigned long long)((float)R.F * md + 0.5f);
+        }
+        // previous-round time as published by CTA 0 (visible one round late)
+        unsigned long long prev_ns = 0;
+        if (r >= 2)
+            prev_ns = pg_ldcg64(&ctrl->round_t[(r - 1) & 3]) - pg_ldcg64(&ctrl->round_t[(r - 2) & 3]);
         float x[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
         if (A.L.schedule == PG_SCHED_LEARNED || A.L.trace != nullptr) {
             x[0] = flog2p1((float)R.F) / 24.f;
@@ -637,34 +861,57 @@ __global__ void __launch_bounds__(512) pg_traverse_kernel(const TravArgs A) {
             pull = false;
             R.tau = 1u << action;
         }
-        if (!pull && A.L.schedule == PG_SCHED_FIXED) R.tau = A.L.tau;
+        // A plain push round on a bag whose entries all carry the same
+        // distance, right after a plain push round, improves each vertex at
+        // most once: no de-duplication tags needed.
+        const bool plain_now = !pull && R.tau == 1u;
+        R.dedupe = kReach || !(plain_now && prev_plain && Lvl == Lmax);
+        prev_plain = plain_now;
         edges_seen += E;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             reset_slot(&ctrl->slot[(r + 2) % PG_NUM_SLOTS]);
-            if (pg_gtimer() > t_deadline) atomicOr(&ctrl->status, PG_DEV_TIMEOUT);
+            ctrl->exp_edges[(r + 2) & 3] = 0;
+            ctrl->exp_verts[(r + 2) & 3] = 0;
+            t_round = pg_gtimer();
+            ctrl->round_t[r & 3] = t_round;
+            if (t_round > t_deadline) atomicOr(&ctrl->status, PG_DEV_TIMEOUT);
         }
 
         // ---- round work
         if (pull) {
-            pull_round(A, R, Lvl, lane, gwarp, nwarps, C);
+            pull_round(A, R, S, Lvl, lane, gwarp, nwarps, C);
             pull_rounds++;
         } else {
-            for (;;) {
-                uint32_t base = 0;
-                if (lane == 0) base = atomicAdd(&R.sc->head, A.L.chunk);
-                base = __shfl_sync(kFull, base, 0);
+            // first task of every warp assigned statically, the rest grabbed
+            const uint32_t span = nwarps * A.L.chunk;
+            for (uint32_t base = gwarp * A.L.chunk;;) {
                 if (base >= R.F) break;
                 const uint32_t c = min(A.L.chunk, R.F - base);
-                const uint32_t entry =
+                uint32_t entry =
                     ((uint32_t)lane < c) ? __ldcg(A.bag + (size_t)R.cur * A.cap + base + lane)
                                          : PG_NONE;
+                entry = PG_DBG_ENTRY(A, entry, 1u, kReach);
                 run_task<kReach>(A, R, S, entry, c, lane, C);
+                if (R.F <= span) break;
+                uint32_t b = 0;
+                if (lane == 0) b = atomicAdd(&R.sc->head, A.L.chunk);
+                base = span + __shfl_sync(kFull, b, 0);
             }
-            hub_edges<kReach>(A, R, lane, C);
+            hub_edges<kReach>(A, R, S, lane, C);
         }
-        ok = pg_grid_sync(ctrl, nblocks, gen, tmo, &s_flag);
-        if (!ok) break;
-        const unsigned long long t_end = __ldcg(&ctrl->t_release);
+        // expansion statistics of this round (mean degree for the next round)
+        {
+            const unsigned long long ee = warp_sum64(C.exp_edges);
+            const unsigned long long ev = warp_sum64((unsigned long long)C.exp_verts);
+            if (lane == 0 && ev) {
+                atomicAdd(&ctrl->exp_edges[r & 3], ee);
+                atomicAdd(&ctrl->exp_verts[r & 3], (unsigned)ev);
+            }
+            C.exp_edges = 0;
+            C.exp_verts = 0;
+        }
+        if (!pg_grid_sync(ctrl, nblocks, gen, tmo, &s_flag)) break;
+        const unsigned long long t_end = pg_gtimer();
 
         // ---- training traces: vertices already at their final distance
         unsigned long long settled = 0;
@@ -674,27 +921,23 @@ __global__ void __launch_bounds__(512) pg_traverse_kernel(const TravArgs A) {
                 cnt += (pg_ldcg(A.dist + v) == __ldg(A.L.ref_dist + v)) ? 1u : 0u;
             cnt = warp_sum64(cnt);
             if (lane == 0 && cnt) atomicAdd(&R.sc->settled, cnt);
-            ok = pg_grid_sync(ctrl, nblocks, gen, tmo, &s_flag);
-            if (!ok) break;
+            if (!pg_grid_sync(ctrl, nblocks, gen, tmo, &s_flag)) break;
             settled = pg_ldcg64(&R.sc->settled);
         }
         if (blockIdx.x == 0 && threadIdx.x == 0 && A.L.trace != nullptr && r < A.L.trace_cap) {
             pg_round_trace tr;
             tr.round = r;
-            tr.action = pull ? PG_ACTION_PULL
-                             : (uint32_t)(31 - __clz((int)max(R.tau, 1u)));
+            tr.action = pull ? PG_ACTION_PULL : (uint32_t)(31 - __clz((int)max(R.tau, 1u)));
             tr.frontier = R.F;
             tr.min_level = Lvl;
             tr.out_edges = E;
-            tr.t_begin_ns = t_begin;
+            tr.t_begin_ns = t_round;
             tr.t_end_ns = t_end;
             tr.settled = settled;
             for (int i = 0; i < 5; i++) tr.features[i] = x[i];
             tr.reserved = 0;
             A.L.trace[r] = tr;
         }
-        prev_ns = t_end - t_begin;
-        t_begin = __ldcg(&ctrl->t_release);
     }
     // ---- totals
     unsigned long long e = C.expansions, p = C.pushes;
@@ -710,16 +953,15 @@ __global__ void __launch_bounds__(512) pg_traverse_kernel(const TravArgs A) {
     }
 }
 
-template <bool kReach>
 size_t traverse_smem(uint32_t threads, uint32_t qcap) {
     const uint32_t nw = threads / 32;
-    return 6144 + (size_t)nw * 256 + (size_t)nw * 96 * 4 + (size_t)nw * qcap * 4;
+    return 6144 + (size_t)nw * 256 + (size_t)nw * (4u * 32u + 2u * kSpillCap + 2u * qcap) * 4u;
 }
 
 template <bool kReach>
 pg_status launch_impl(pg_graph *g, PgLaunch &L, TravArgs &A, cudaStream_t s) {
     auto kern = pg_traverse_kernel<kReach>;
-    const size_t smem = traverse_smem<kReach>(L.threads, L.qcap);
+    const size_t smem = traverse_smem(L.threads, L.qcap);
     int maxopt = 0;
     PG_CK(cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device));
     if (smem > (size_t)maxopt)
@@ -733,14 +975,16 @@ pg_status launch_impl(pg_graph *g, PgLaunch &L, TravArgs &A, cudaStream_t s) {
         return pg_set_error(PG_ERR_INVALID_ARG,
                             "launch shape does not fit an SM (threads=%u, local_queue=%u)",
                             L.threads, L.qcap);
-    uint32_t bps = L.blocks ? min((uint32_t)per_sm, L.blocks) : (uint32_t)per_sm;
+    const uint32_t bps = L.blocks ? min((uint32_t)per_sm, L.blocks) : (uint32_t)per_sm;
     const uint32_t grid = bps * (uint32_t)g->num_sms;
     L.blocks = bps;
     A.L = L;
     PG_CK(cudaMemsetAsync(g->d_ctrl, 0, sizeof(PgCtrl), s));
     void *args[] = {(void *)&A};
+    PG_CK(cudaEventRecord(g->ev0, s));
     PG_CK(cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(L.threads), args, smem,
                                       s));
+    PG_CK(cudaEventRecord(g->ev1, s));
     return PG_OK;
 }
 
@@ -757,6 +1001,10 @@ pg_status pg_launch_traverse(pg_graph *g, PgLaunch &L, int kind, uint32_t src,
     A.G.tidx = g->d_tidx ? g->d_tidx : g->d_idx;
     A.G.n = g->n;
     A.G.m = g->m;
+    A.ell0 = g->d_ell[0];
+    A.ellw0 = g->d_ell[0] ? g->ellw[0] : 0u;
+    A.ell1 = g->d_ell[1];
+    A.ellw1 = g->d_ell[1] ? g->ellw[1] : 0u;
     A.ctrl = g->d_ctrl;
     A.bag = g->d_bag;
     A.cap = g->bag_cap;
@@ -764,11 +1012,16 @@ pg_status pg_launch_traverse(pg_graph *g, PgLaunch &L, int kind, uint32_t src,
     A.hubs = g->d_hubs;
     A.hcap = g->hub_cap;
     A.dist = dist;
-    A.mask[0] = fwd;
-    A.mask[1] = bwd;
+    A.mask0 = fwd;
+    A.mask1 = bwd;
     A.src = src;
     A.k = k;
     A.dir = dir;
+    A.need_deg = (kind == 0 && L.schedule == PG_SCHED_FIXED && L.direction == PG_DIR_AUTO &&
+                  L.allow_pull) ? 1u : 0u;
+    const uint32_t md =
+        (kind == 1 && (dir & PG_BWD)) ? max(g->maxdeg[0], g->maxdeg[1]) : g->maxdeg[0];
+    A.hubs_possible = md >= L.hub_degree ? 1u : 0u;
     for (uint32_t j = 0; j < k && j < 64; j++) A.sources[j] = sources[j];
     if (kind == 0) return launch_impl<false>(g, L, A, s);
     return launch_impl<true>(g, L, A, s);

@@ -68,9 +68,10 @@ def _tiny():
     return out
 
 
-def test_tiny_graphs_all_sources(pg):
+@pytest.mark.parametrize("ell", [True, False])
+def test_tiny_graphs_all_sources(pg, ell):
     for g in _tiny():
-        G = pg.Graph.from_graphgen(g)
+        G = pg.Graph.from_graphgen(g, ell=ell)
         D = oracle.floyd_warshall(g) if g.n <= 64 else None
         for s in range(0, g.n, max(1, g.n // 9)):
             want = oracle.bfs(g, s)
@@ -88,22 +89,25 @@ def test_tiny_graphs_all_sources(pg):
     ("rmat", lambda: gg.rmat(16, 16, 3), False),
     ("dgrid", lambda: gg.dgrid(301, 277, 4), True),
 ])
-def test_medium_vs_oracle(pg, name, make, directed):
+@pytest.mark.parametrize("ell", [True, False])
+def test_medium_vs_oracle(pg, name, make, directed, ell):
     g = make()
-    G = pg.Graph.from_graphgen(g)
+    G = pg.Graph.from_graphgen(g, ell=ell)
     srcs = gg.pick_sources(g, 3, 7)
     for s in srcs:
         want = oracle.bfs(g, s)
         for kw in ({"tau": 1}, {"tau": 4, "chunk": 8}, {"tau": 32, "local_queue": 128},
                    {"tau": 16, "hub_degree": 64}, {"tau": 1, "direction": 1},
-                   {"tau": 8, "direction": 1, "threads_per_block": 256, "blocks_per_sm": 1}):
+                   {"tau": 8, "direction": 1, "threads_per_block": 256, "blocks_per_sm": 1},
+                   {"tau": 64, "chunk": 2, "local_queue": 32}):
             d, st = _bfs(pg, G, int(s), **kw)
             assert _first_diff(d, want) is None, (name, int(s), kw, _first_diff(d, want))
 
 
-def test_schedule_independence_fuzz(pg):
+@pytest.mark.parametrize("make", [lambda: gg.knn(60_000, 4, 9), lambda: gg.rmat(14, 8, 2)])
+def test_schedule_independence_fuzz(pg, make):
     """Any per-round action sequence gives the same exact distances."""
-    g = gg.knn(60_000, 4, 9)
+    g = make()
     G = pg.Graph.from_graphgen(g)
     want = oracle.bfs(g, 5)
     rng = np.random.default_rng(0)

@@ -38,11 +38,12 @@ def test_tiny_vs_warshall(pg):
                 assert not np.any(f & hi) and not np.any(b & hi)
 
 
+@pytest.mark.parametrize("ell", [True, False])
 @pytest.mark.parametrize("tau,kw", [(1, {}), (16, {}), (64, {"chunk": 4}),
                                      (8, {"hub_degree": 32, "local_queue": 64})])
-def test_dgrid_fwd_bwd(pg, tau, kw):
+def test_dgrid_fwd_bwd(pg, tau, kw, ell):
     g = gg.dgrid(211, 199, 4)
-    G = pg.Graph.from_graphgen(g)
+    G = pg.Graph.from_graphgen(g, ell=ell)
     srcs = gg.pick_sources(g, 64, 2)
     f, b = _reach(pg, G, srcs, pg.PG_FWD | pg.PG_BWD, tau=tau, **kw)
     assert np.array_equal(f, oracle.reach(g, srcs))
