@@ -234,7 +234,7 @@ def main():
     out = torch.empty(g.n, dtype=torch.int32, device="cuda")
 
     # --- forms: plain fixed tau (autotuned) and learned schedule
-    plain_cfg = pg.default_config(tau=16, chunk=8, blocks_per_sm=1)
+    plain_cfg = pg.default_config(tau=16, chunk=2, blocks_per_sm=1)
     tuned = None
     if not args.no_autotune:
         t0 = time.perf_counter()

@@ -45,7 +45,7 @@ typedef enum pg_status {
 #define PG_DIRECTED 1u        /* arcs as given; otherwise the CSR must be symmetric */
 #define PG_BUILD_TRANSPOSE 2u /* build the reversed CSR on the device (pull, backward reach) */
 #define PG_SKIP_VALIDATE 4u   /* trust the CSR (skips the validation kernel) */
-#define PG_NO_ELL 8u          /* do not build padded adjacency rows (CSR only) */
+#define PG_ELL 8u             /* also build padded adjacency rows (see pg_graph_upload) */
 
 /* pg_reach_multi directions */
 #define PG_FWD 1u
@@ -98,7 +98,7 @@ typedef struct pg_config {
     uint32_t blocks_per_sm;     /* persistent CTAs per SM; 0 = as many as fit */
     uint32_t threads_per_block; /* 64..512, multiple of 32; 0 = 512 */
     uint32_t local_queue;       /* per-warp shared-memory queue entries, power of two 32..4096; 0 = 512 */
-    uint32_t chunk;             /* frontier entries one warp takes per task (1..32); 0 = 32 */
+    uint32_t chunk;             /* frontier entries one warp takes per task (1..32); 0 = 2 */
     uint32_t hub_degree;        /* out-degree from which a vertex's edges are split across warps; 0 = 2048 */
     uint32_t timeout_ms;        /* limit for every device-side wait; 0 = 5000 */
     uint32_t max_rounds;        /* 0 = unlimited */
@@ -123,19 +123,21 @@ typedef struct pg_stats {
     uint32_t reserved;
 } pg_stats;
 
-/* Fill *cfg with defaults (fixed schedule, tau = 16, push only, alpha 15, beta 18). */
+/* Fill *cfg with defaults (fixed schedule, tau = 16, chunk 2, push only, alpha 15, beta 18). */
 void pg_config_default(pg_config *cfg);
 
 /*
  * Upload a graph (Sec. 2 preliminaries: G = (V, E), n = |V|, m = |E|).
  *  offsets[n+1], indices[m]: CSR, host or device memory (detected); copied,
  *    so the caller may free them afterwards.  Lists need not be sorted.
- *  flags: PG_DIRECTED, PG_BUILD_TRANSPOSE, PG_SKIP_VALIDATE, PG_NO_ELL.
- *  When at most 0.1% of the vertices have more than 16 out-neighbours, the
- *    library also keeps padded rows (4, 8 or 16 ids per vertex, the smallest
- *    width that 99.9% of the vertices fit) so that a traversal step reads a
- *    neighbour list with 16-byte loads and no offsets lookup; longer lists
- *    stay in the CSR.  PG_NO_ELL turns this off.
+ *  flags: PG_DIRECTED, PG_BUILD_TRANSPOSE, PG_SKIP_VALIDATE, PG_ELL.
+ *  PG_ELL: when at most 0.1% of the vertices have more than 16
+ *    out-neighbours, also keep padded rows (4, 8 or 16 ids per vertex, the
+ *    smallest width that 99.9% of the vertices fit) so that a traversal step
+ *    reads a neighbour list with 16-byte loads and no offsets lookup; longer
+ *    lists stay in the CSR.  Measured slower than the CSR path on GB300 for
+ *    now (more instructions per step than the saved offsets load), so it is
+ *    opt-in.
  *  Validation (unless skipped): offsets[0] = 0, non-decreasing, offsets[n] = m,
  *    every index < n; failure -> PG_ERR_INVALID_GRAPH.
  *  *out receives a library-owned handle; free it with pg_graph_free.

@@ -24,7 +24,7 @@ PG_ERR_CUDA, PG_ERR_TIMEOUT, PG_ERR_UNSUPPORTED, PG_ERR_OVERFLOW = 4, 5, 6, 7
 STATUS_NAMES = {0: "PG_OK", 1: "PG_ERR_INVALID_ARG", 2: "PG_ERR_INVALID_GRAPH", 3: "PG_ERR_OOM",
                 4: "PG_ERR_CUDA", 5: "PG_ERR_TIMEOUT", 6: "PG_ERR_UNSUPPORTED",
                 7: "PG_ERR_OVERFLOW"}
-PG_DIRECTED, PG_BUILD_TRANSPOSE, PG_SKIP_VALIDATE, PG_NO_ELL = 1, 2, 4, 8
+PG_DIRECTED, PG_BUILD_TRANSPOSE, PG_SKIP_VALIDATE, PG_ELL = 1, 2, 4, 8
 PG_FWD, PG_BWD = 1, 2
 PG_SCHED_FIXED, PG_SCHED_LEARNED, PG_SCHED_RANDOM, PG_SCHED_SCRIPT = 0, 1, 2, 3
 PG_DIR_PUSH, PG_DIR_AUTO = 0, 1
@@ -159,7 +159,7 @@ class Graph:
 
     @classmethod
     def upload(cls, offsets, indices, directed: bool = False, transpose: bool = True,
-               validate: bool = True, ell: bool = True, stream=None) -> "Graph":
+               validate: bool = True, ell: bool = False, stream=None) -> "Graph":
         """Copy a CSR (numpy host arrays or CUDA tensors) into library-owned memory."""
         lib = load()
         po, ko = _u32_array(offsets)
@@ -169,8 +169,8 @@ class Graph:
         flags = (PG_DIRECTED if directed else 0) | (PG_BUILD_TRANSPOSE if (directed and transpose) else 0)
         if not validate:
             flags |= PG_SKIP_VALIDATE
-        if not ell:
-            flags |= PG_NO_ELL
+        if ell:
+            flags |= PG_ELL
         h = ctypes.c_void_p()
         _check(lib.pg_graph_upload(po, pi, n, m, flags, _stream_ptr(stream), ctypes.byref(h)))
         return cls(h, n, m, directed)

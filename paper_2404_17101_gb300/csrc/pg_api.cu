@@ -56,6 +56,7 @@ extern "C" void pg_config_default(pg_config *c) {
     c->struct_size = sizeof(pg_config);
     c->schedule = PG_SCHED_FIXED;
     c->tau = 16;
+    c->chunk = 2;
     c->direction = PG_DIR_PUSH;
     c->alpha = 15;
     c->beta = 18;
@@ -84,7 +85,7 @@ pg_status pg_resolve_config(pg_graph *g, const pg_config *cfg, PgLaunch *L) {
     L->qcap = c->local_queue ? c->local_queue : 512;
     if (L->qcap < 32 || L->qcap > 4096 || (L->qcap & (L->qcap - 1)))
         return pg_set_error(PG_ERR_INVALID_ARG, "local_queue %u must be a power of two in 32..4096", L->qcap);
-    L->chunk = c->chunk ? c->chunk : 32;
+    L->chunk = c->chunk ? c->chunk : 2;
     if (L->chunk > 32) return pg_set_error(PG_ERR_INVALID_ARG, "chunk %u > 32", L->chunk);
     L->hub_degree = c->hub_degree ? c->hub_degree : 2048;
     if (L->hub_degree < 32) return pg_set_error(PG_ERR_INVALID_ARG, "hub_degree %u < 32", L->hub_degree);
@@ -448,14 +449,14 @@ extern "C" pg_status pg_graph_upload(const uint32_t *offsets, const uint32_t *in
         g->has_transpose = true;
         g->transpose_is_self = true;
     }
-    PG_TRY(build_rows(g, 0, !(flags & PG_NO_ELL), s));
+    PG_TRY(build_rows(g, 0, (flags & PG_ELL) != 0, s));
     if (g->has_transpose) {
         if (g->transpose_is_self) {
             g->d_ell[1] = g->d_ell[0];
             g->ellw[1] = g->ellw[0];
             g->maxdeg[1] = g->maxdeg[0];
         } else {
-            PG_TRY(build_rows(g, 1, !(flags & PG_NO_ELL), s));
+            PG_TRY(build_rows(g, 1, (flags & PG_ELL) != 0, s));
         }
     }
     PG_TRY(alloc_workspace(g, 2048, s));
@@ -497,7 +498,7 @@ extern "C" pg_status pg_graph_set_transpose(pg_graph *g, const uint32_t *t_offse
     g->d_tidx = tidx;
     g->has_transpose = true;
     g->transpose_is_self = false;
-    st = build_rows(g, 1, !(g->flags & PG_NO_ELL), s);
+    st = build_rows(g, 1, (g->flags & PG_ELL) != 0, s);
     if (st) return st;
     PG_CK(cudaStreamSynchronize(s));
     return PG_OK;

@@ -71,7 +71,7 @@ extern "C" pg_status pg_autotune(pg_graph *g, uint32_t kind, const uint32_t *sou
     // warm-up and baseline
     st = measure(best, &best_ms);
     const uint32_t taus[] = {1, 2, 4, 8, 16, 32, 64};
-    const uint32_t chunks[] = {4, 8, 16, 32};
+    const uint32_t chunks[] = {1, 2, 4, 8, 32};
     const uint32_t queues[] = {128, 512, 2048};
     const uint32_t threads[] = {256, 512};
     const uint32_t bps[] = {1, 2, 3, 4};
@@ -80,7 +80,7 @@ extern "C" pg_status pg_autotune(pg_graph *g, uint32_t kind, const uint32_t *sou
         int nv;
         switch (knob) {
             case 0: vals = taus; nv = 7; break;
-            case 1: vals = chunks; nv = 4; break;
+            case 1: vals = chunks; nv = 5; break;
             case 2: vals = queues; nv = 3; break;
             case 3: vals = threads; nv = 2; break;
             default: vals = bps; nv = 4; break;
