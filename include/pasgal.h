@@ -228,6 +228,30 @@ pg_status pg_mlp_adam(float *params, const float *grad, float *m, float *v, uint
 pg_status pg_autotune(pg_graph *g, uint32_t kind, const uint32_t *sources, uint32_t k,
                       uint32_t dir, uint32_t trials, pg_config *cfg, void *stream);
 
+/*
+ * Single-source BFS that allocates nothing.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * when they call, e.g. inside a framework whose memory pool owns the whole
+ * device, or in a latency-bound loop where cudaMalloc's implicit device
+ * synchronisation is not allowed.  Same result as pg_graph_upload + pg_bfs.
+ *  offsets[n+1], indices[m], dist_out[n]: caller-owned DEVICE memory (the
+ *    CSR is validated like pg_graph_upload; invalid -> PG_ERR_INVALID_GRAPH).
+ *  n must be 1..PG_NOALLOC_MAX_N (larger -> PG_ERR_INVALID_ARG, nothing run).
+ *  cfg: NULL or a fixed push schedule (tau, chunk, launch shape, timeout);
+ *    learned/scripted schedules, pull rounds and traces -> PG_ERR_UNSUPPORTED.
+ *    High-degree vertices are not split across warps here.
+ *  Scratch lives in a fixed array of PG_NOALLOC_SCRATCH_BYTES compiled into
+ *    the library (held by every GPU that loads it until exit) and shared by
+ *    all calls on a device: calls that overlap on the GPU race, so serialise
+ *    them per device.  The first call on a device looks up the array's
+ *    address (cudaGetSymbolAddress); make it before any stream capture.
+ *  No cudaMalloc, cudaFree or allocating library routine is called.
+ */
+#define PG_NOALLOC_MAX_N (1u << 20)
+#define PG_NOALLOC_SCRATCH_BYTES (13u << 20)
+pg_status pg_bfs_noalloc(const uint32_t *offsets, const uint32_t *indices, uint32_t n, uint32_t m,
+                         uint32_t src, uint32_t *dist_out, const pg_config *cfg, void *stream);
+
 /* Thread-local message for the last failing call on this thread ("" if none). */
 const char *pg_last_error(void);
 

@@ -36,7 +36,8 @@ INF = 0xFFFFFFFF
 EXPORTS = ["pg_config_default", "pg_graph_upload", "pg_graph_set_transpose", "pg_graph_free",
            "pg_graph_info", "pg_bfs", "pg_reach_multi", "pg_bfs_multi", "pg_count_reached",
            "pg_set_schedule_weights", "pg_mlp_forward", "pg_mlp_backward", "pg_mlp_adam",
-           "pg_autotune", "pg_last_error", "pg_version"]
+           "pg_autotune", "pg_bfs_noalloc", "pg_last_error", "pg_version"]
+NOALLOC_MAX_N = 1 << 20
 
 
 class PgError(RuntimeError):
@@ -107,6 +108,7 @@ def load(path: str | None = None):
         "pg_mlp_adam": (ctypes.c_int, [vp, vp, vp, vp, u32, u32, ctypes.c_float, ctypes.c_float,
                                        ctypes.c_float, ctypes.c_float, vp]),
         "pg_autotune": (ctypes.c_int, [vp, u32, vp, u32, u32, u32, P(Config), vp]),
+        "pg_bfs_noalloc": (ctypes.c_int, [vp, vp, u32, u32, u32, vp, P(Config), vp]),
         "pg_last_error": (ctypes.c_char_p, []),
         "pg_version": (ctypes.c_char_p, []),
     }
@@ -294,6 +296,19 @@ def mlp_adam(params, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, s
     _check(load().pg_mlp_adam(ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(grad.data_ptr()),
                               ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(v.data_ptr()),
                               params.numel(), t, lr, beta1, beta2, eps, _stream_ptr(stream)))
+
+
+def bfs_noalloc(offsets, indices, src: int, out, cfg: Config | None = None, stream=None):
+    """pg_bfs_noalloc on caller-owned CUDA tensors (int32 views of uint32).
+
+    For callers that cannot allocate device memory at call time: the library
+    uses a fixed scratch array instead of allocating.  offsets/indices/out
+    must already live on the device; n <= NOALLOC_MAX_N."""
+    n = offsets.numel() - 1
+    _check(load().pg_bfs_noalloc(ctypes.c_void_p(offsets.data_ptr()), ctypes.c_void_p(indices.data_ptr()),
+                                 n, indices.numel(), int(src), ctypes.c_void_p(out.data_ptr()),
+                                 ctypes.byref(cfg) if cfg else None, _stream_ptr(stream)))
+    return out
 
 
 def version() -> str:

@@ -209,3 +209,17 @@ pg_status pg_launch_traverse(pg_graph *g, PgLaunch &L, int kind, uint32_t src,
                              cudaStream_t s);
 pg_status pg_launch_msbfs(pg_graph *g, PgLaunch &L, const uint32_t *sources, uint32_t k,
                           uint32_t *dist, cudaStream_t s);
+
+// BFS launch on caller-provided workspace (used by the allocation-free entry
+// point): CSR, output and every scratch buffer are given as raw pointers.
+struct PgRawBfs {
+    const uint32_t *off, *idx;
+    uint32_t n, m, src;
+    uint32_t *dist;
+    PgCtrl *ctrl;
+    uint32_t *bag;    // 2 * cap entries
+    uint32_t cap;
+    uint32_t *stamp;  // n entries
+    int device, num_sms;
+};
+pg_status pg_launch_bfs_raw(const PgRawBfs &w, PgLaunch &L, cudaStream_t s);

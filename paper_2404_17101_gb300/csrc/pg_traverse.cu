@@ -990,6 +990,49 @@ pg_status launch_impl(pg_graph *g, PgLaunch &L, TravArgs &A, cudaStream_t s) {
 
 }  // namespace
 
+pg_status pg_launch_bfs_raw(const PgRawBfs &w, PgLaunch &L, cudaStream_t s) {
+    TravArgs A;
+    memset(&A, 0, sizeof(A));
+    A.G.off = w.off;
+    A.G.idx = w.idx;
+    A.G.toff = w.off;   // push only: the reverse lists are never read
+    A.G.tidx = w.idx;
+    A.G.n = w.n;
+    A.G.m = w.m;
+    A.ctrl = w.ctrl;
+    A.bag = w.bag;
+    A.cap = w.cap;
+    A.stamp = w.stamp;
+    A.hubs = nullptr;
+    A.hcap = 0;
+    A.dist = w.dist;
+    A.src = w.src;
+    A.need_deg = 0;
+    A.hubs_possible = 0;
+    auto kern = pg_traverse_kernel<false>;
+    const size_t smem = traverse_smem(L.threads, L.qcap);
+    int maxopt = 0;
+    PG_CK(cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, w.device));
+    if (smem > (size_t)maxopt)
+        return pg_set_error(PG_ERR_INVALID_ARG,
+                            "launch shape needs %zu B shared memory > %d (threads=%u, local_queue=%u)",
+                            smem, maxopt, L.threads, L.qcap);
+    PG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)L.threads, smem));
+    if (per_sm < 1)
+        return pg_set_error(PG_ERR_INVALID_ARG, "launch shape does not fit an SM (threads=%u, local_queue=%u)",
+                            L.threads, L.qcap);
+    const uint32_t bps = L.blocks ? min((uint32_t)per_sm, L.blocks) : (uint32_t)per_sm;
+    L.blocks = bps;
+    A.L = L;
+    PG_CK(cudaMemsetAsync(w.ctrl, 0, sizeof(PgCtrl), s));
+    void *args[] = {(void *)&A};
+    PG_CK(cudaLaunchCooperativeKernel((const void *)kern, dim3(bps * (uint32_t)w.num_sms),
+                                      dim3(L.threads), args, smem, s));
+    return PG_OK;
+}
+
 pg_status pg_launch_traverse(pg_graph *g, PgLaunch &L, int kind, uint32_t src,
                              const uint32_t *sources, uint32_t k, uint32_t dir, uint32_t *dist,
                              unsigned long long *fwd, unsigned long long *bwd, cudaStream_t s) {
