@@ -1,0 +1,191 @@
+"""Train the per-round schedule network from traces of the traversal.
+
+The paper fixes one tau per run (Sec. 2.1, "tau ... is a tunable
+parameter") and names direction optimisation (Sec. 2.2) without a policy.
+Here a small network picks, every round, one of 8 actions (push with
+tau = 1, 2, 4, ..., 64, or a pull round) from five statistics of the round
+(frontier size, its out-edges, their mean degree, round index, recent round
+time).  It never changes the result (every schedule reaches the same exact
+fixpoint); it only changes how fast the fixpoint is reached.
+
+Training signal (a contextual bandit): for seeded graphs from the training
+families, the plain traversal (tau = 1) first gives the final distances.
+Runs with uniformly random actions then record, for every round, the
+features, the action, the round time and how many vertices hold their final
+distance after it.  The network regresses log2(1 + vertices settled per
+microsecond) for the action taken; at run time the traversal takes the
+arg-max action.  Forward, backward and Adam run in the library's own CUDA
+kernels (pg_mlp_forward / pg_mlp_backward / pg_mlp_adam).
+
+    python -m paper_2404_17101_gb300.train_schedule --out schedule_mlp.f32 [--quick]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import graphgen as gg  # noqa: E402
+import paper_2404_17101_gb300 as pg  # noqa: E402
+
+INF = 0xFFFFFFFF
+
+
+def training_graphs(quick: bool):
+    """Seeded training families: grids (aspect 1:1 .. 1:1000), kNN (k 2..10), R-MAT."""
+    fams = [
+        ("grid_1000x1000", lambda: gg.grid(1000, 1000)),
+        ("grid_300x3000", lambda: gg.grid(300, 3000)),
+        ("grid_60x60000", lambda: gg.grid(60, 60000)),
+        ("knn_1m_k5", lambda: gg.knn(1_000_000, 5, 101)),
+        ("knn_1m_k3", lambda: gg.knn(1_000_000, 3, 102)),
+        ("knn_500k_k8", lambda: gg.knn(500_000, 8, 103)),
+        ("rmat_17", lambda: gg.rmat(17, 16, 104)),
+    ]
+    if not quick:
+        fams += [
+            ("grid_2000x2000", lambda: gg.grid(2000, 2000)),
+            ("grid_126x31700", lambda: gg.grid(126, 31700)),
+            ("grid_2x400000", lambda: gg.grid(2, 400_000)),
+            ("knn_4m_k5", lambda: gg.knn(4_000_000, 5, 105)),
+            ("knn_2m_k2", lambda: gg.knn(2_000_000, 2, 106)),
+            ("knn_2m_k10", lambda: gg.knn(2_000_000, 10, 107)),
+            ("knn_3m_k4", lambda: gg.knn(3_000_000, 4, 108)),
+            ("rmat_18", lambda: gg.rmat(18, 16, 109)),
+            ("rmat_20", lambda: gg.rmat(20, 16, 110)),
+        ]
+    return fams
+
+
+def collect(G, src, seeds, chunk=2, cap=400_000):
+    """Per-round samples (features, action, target) from random-schedule runs."""
+    import torch
+    ref = G.bfs(src, cfg=pg.default_config(tau=1, chunk=chunk))
+    unreach = int((ref == -1).sum().item())
+    Xs, As, Ys = [], [], []
+    for seed in seeds:
+        buf = (pg.RoundTrace * cap)()
+        cfg = pg.default_config(schedule=pg.PG_SCHED_RANDOM, seed=seed, chunk=chunk, trace_cap=cap)
+        cfg.trace_out = buf
+        cfg.ref_dist = ref.data_ptr()
+        st = pg.Stats()
+        out = G.bfs(src, cfg=cfg, stats=st)
+        if not torch.equal(out, ref):
+            raise RuntimeError("random schedule changed the distances")
+        R = min(st.rounds, cap)
+        prev = 1 + unreach
+        for r in range(R):
+            t = buf[r]
+            dt_us = max((t.t_end_ns - t.t_begin_ns) / 1000.0, 0.5)
+            prog = max(int(t.settled) - prev, 0)
+            prev = int(t.settled)
+            Xs.append(list(t.features))
+            As.append(int(t.action))
+            Ys.append(math.log2(1.0 + prog / dt_us))
+    return (np.asarray(Xs, np.float32), np.asarray(As, np.uint32), np.asarray(Ys, np.float32))
+
+
+def init_params(seed=0):
+    rng = np.random.default_rng(seed)
+    p = []
+    for fan_out, fan_in in ((32, 5), (32, 32), (8, 32)):
+        p.append(rng.normal(0, math.sqrt(2.0 / fan_in), size=fan_out * fan_in))
+        p.append(np.zeros(fan_out))
+    return np.concatenate(p).astype(np.float32)
+
+
+def train(X, A, Y, epochs=60, batch=4096, lr=3e-3, seed=0, log=print):
+    """Mini-batch Adam on the GPU with the library's MLP kernels."""
+    import torch
+    dev = "cuda"
+    mu, sd = float(Y.mean()), float(Y.std() + 1e-6)
+    Xd = torch.from_numpy(X).to(dev)
+    Ad = torch.from_numpy(A.view(np.int32)).to(dev)
+    Yd = torch.from_numpy(((Y - mu) / sd).astype(np.float32)).to(dev)
+    P = torch.from_numpy(init_params(seed)).to(dev)
+    m = torch.zeros_like(P)
+    v = torch.zeros_like(P)
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    N = X.shape[0]
+    t = 0
+    for ep in range(epochs):
+        perm = torch.randperm(N, generator=g).to(dev)
+        tot = 0.0
+        for b0 in range(0, N, batch):
+            idx = perm[b0:b0 + batch]
+            xb, ab, yb = Xd[idx].contiguous(), Ad[idx].contiguous(), Yd[idx].contiguous()
+            loss, grad = pg.mlp_backward(P, xb, ab, yb)
+            t += 1
+            pg.mlp_adam(P, grad, m, v, t, lr=lr)
+            tot += float(loss.item()) * len(idx)
+        if ep % 10 == 0 or ep == epochs - 1:
+            log(f"epoch {ep:3d}  loss {tot / N:.4f}")
+    return P.cpu().numpy(), mu, sd
+
+
+def evaluate(G, src, weights, taus=(1, 4, 16, 64), reps=3):
+    """Kernel time of the learned schedule and of fixed-tau schedules."""
+    res = {}
+    G.set_schedule_weights(weights)
+    forms = {f"tau{t}": pg.default_config(tau=t) for t in taus}
+    forms["learned"] = pg.default_config(schedule=pg.PG_SCHED_LEARNED)
+    for name, cfg in forms.items():
+        st = pg.Stats()
+        G.bfs(src, cfg=cfg, stats=st)
+        ts = []
+        for _ in range(reps):
+            G.bfs(src, cfg=cfg, stats=st)
+            ts.append(st.kernel_ms)
+        res[name] = {"ms": min(ts), "rounds": st.rounds}
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                                  "schedule_mlp.f32"))
+    ap.add_argument("--quick", action="store_true")
+    ap.add_argument("--runs", type=int, default=4)
+    ap.add_argument("--epochs", type=int, default=60)
+    ap.add_argument("--log", default=None)
+    args = ap.parse_args()
+    import torch
+    torch.cuda.set_device(0)
+    pg.load()
+    lines = []
+
+    def log(s):
+        print(s, flush=True)
+        lines.append(s)
+
+    Xs, As, Ys = [], [], []
+    t0 = time.time()
+    for name, make in training_graphs(args.quick):
+        g = make()
+        G = pg.Graph.from_graphgen(g)
+        for si, src in enumerate(gg.pick_sources(g, 2, 7)):
+            X, A, Y = collect(G, int(src), seeds=[1000 * si + r for r in range(args.runs)])
+            Xs.append(X); As.append(A); Ys.append(Y)
+            log(f"{name} src={int(src)} rounds={len(Y)}")
+        G.free()
+    X, A, Y = np.concatenate(Xs), np.concatenate(As), np.concatenate(Ys)
+    log(f"samples {len(Y)}  collected in {time.time() - t0:.1f}s")
+    W, mu, sd = train(X, A, Y, epochs=args.epochs, log=log)
+    W.astype(np.float32).tofile(args.out)
+    log(f"weights -> {args.out}")
+    if args.log:
+        with open(args.log, "w") as f:
+            json.dump({"lines": lines, "samples": int(len(Y)), "target_mean": mu, "target_std": sd}, f)
+
+
+if __name__ == "__main__":
+    main()
