@@ -248,21 +248,20 @@ def main():
     G = pg.Graph.from_graphgen(g)
     out = torch.empty(g.n, dtype=torch.int32, device="cuda")
 
-    # --- forms: plain fixed tau (autotuned) and learned schedule
-    plain_cfg = pg.default_config(tau=16, chunk=2, blocks_per_sm=1)
+    # --- forms: the plain fixed-tau traversal (library defaults), the same
+    # with tau and launch shape picked by the autotuner for this graph, and
+    # the learned per-round schedule (when trained weights exist)
+    plain_cfg = pg.default_config()
+    forms = {"plain": plain_cfg}
     tuned = None
     if not args.no_autotune:
         t0 = time.perf_counter()
-        plain_cfg = G.autotune([src], kind=0, trials=3, cfg=plain_cfg)
+        forms["plain_tuned"] = G.autotune([src], kind=0, trials=3, cfg=pg.default_config())
         tuned = time.perf_counter() - t0
-    forms = {"plain": plain_cfg}
     w = pg.trained_weights()
     if w is not None:
         G.set_schedule_weights(w)
-        lc = pg.default_config(schedule=pg.PG_SCHED_LEARNED)
-        for f in ("chunk", "local_queue", "threads_per_block", "blocks_per_sm"):
-            setattr(lc, f, getattr(plain_cfg, f))
-        forms["learned"] = lc
+        forms["learned"] = pg.default_config(schedule=pg.PG_SCHED_LEARNED)
 
     G.bfs(src, out=out, cfg=plain_cfg)
     n_r, m_r = G.count_reached(out)

@@ -8,14 +8,16 @@ tau = 1, 2, 4, ..., 64, or a pull round) from five statistics of the round
 time).  It never changes the result (every schedule reaches the same exact
 fixpoint); it only changes how fast the fixpoint is reached.
 
-Training signal (a contextual bandit): for seeded graphs from the training
-families, the plain traversal (tau = 1) first gives the final distances.
-Runs with uniformly random actions then record, for every round, the
-features, the action, the round time and how many vertices hold their final
-distance after it.  The network regresses log2(1 + vertices settled per
-microsecond) for the action taken; at run time the traversal takes the
-arg-max action.  Forward, backward and Adam run in the library's own CUDA
-kernels (pg_mlp_forward / pg_mlp_backward / pg_mlp_adam).
+Training signal (rollouts of the traversal itself): on seeded graphs from
+the training families, a base run with a fixed tau is timed; then, at
+sampled rounds r of that run, the traversal is re-run with the base schedule
+up to round r and one action held for every later round, for each of the 8
+actions.  Each rerun records the five features of round r.  The label of
+action a at that state is -log2(T_a / min_b T_b), T = kernel time of the
+whole run, so the network learns which action is best from here on; the
+traversal re-decides every round and takes the arg-max (one step of policy
+improvement over the fixed-tau base).  Forward, backward and Adam run in the
+library's own CUDA kernels (pg_mlp_forward / pg_mlp_backward / pg_mlp_adam).
 
     python -m paper_2404_17101_gb300.train_schedule --out schedule_mlp.f32 [--quick]
 """
@@ -45,7 +47,7 @@ def training_graphs(quick: bool):
     fams = [
         ("grid_1000x1000", lambda: gg.grid(1000, 1000)),
         ("grid_300x3000", lambda: gg.grid(300, 3000)),
-        ("grid_60x60000", lambda: gg.grid(60, 60000)),
+        ("grid_60x20000", lambda: gg.grid(60, 20000)),
         ("knn_1m_k5", lambda: gg.knn(1_000_000, 5, 101)),
         ("knn_1m_k3", lambda: gg.knn(1_000_000, 3, 102)),
         ("knn_500k_k8", lambda: gg.knn(500_000, 8, 103)),
@@ -54,8 +56,8 @@ def training_graphs(quick: bool):
     if not quick:
         fams += [
             ("grid_2000x2000", lambda: gg.grid(2000, 2000)),
-            ("grid_126x31700", lambda: gg.grid(126, 31700)),
-            ("grid_2x400000", lambda: gg.grid(2, 400_000)),
+            ("grid_126x16000", lambda: gg.grid(126, 16000)),
+            ("grid_4x100000", lambda: gg.grid(4, 100_000)),
             ("knn_4m_k5", lambda: gg.knn(4_000_000, 5, 105)),
             ("knn_2m_k2", lambda: gg.knn(2_000_000, 2, 106)),
             ("knn_2m_k10", lambda: gg.knn(2_000_000, 10, 107)),
@@ -66,31 +68,43 @@ def training_graphs(quick: bool):
     return fams
 
 
-def collect(G, src, seeds, chunk=2, cap=400_000):
-    """Per-round samples (features, action, target) from random-schedule runs."""
+def collect(G, src, base_tau=8, points=10, reps=2, hold=80_000):
+    """Rollout samples (features of round r, action, label) for one source."""
     import torch
-    ref = G.bfs(src, cfg=pg.default_config(tau=1, chunk=chunk))
-    unreach = int((ref == -1).sum().item())
+    base_a = int(round(math.log2(base_tau)))
+    st = pg.Stats()
+    ref = G.bfs(src, cfg=pg.default_config(tau=base_tau))
+    R = None
+    for _ in range(reps):
+        G.bfs(src, cfg=pg.default_config(tau=base_tau), stats=st)
+        R = st.rounds
+    rs = sorted(set(int(R * f) for f in np.linspace(0.0, 0.9, points)))
     Xs, As, Ys = [], [], []
-    for seed in seeds:
-        buf = (pg.RoundTrace * cap)()
-        cfg = pg.default_config(schedule=pg.PG_SCHED_RANDOM, seed=seed, chunk=chunk, trace_cap=cap)
-        cfg.trace_out = buf
-        cfg.ref_dist = ref.data_ptr()
-        st = pg.Stats()
-        out = G.bfs(src, cfg=cfg, stats=st)
-        if not torch.equal(out, ref):
-            raise RuntimeError("random schedule changed the distances")
-        R = min(st.rounds, cap)
-        prev = 1 + unreach
-        for r in range(R):
-            t = buf[r]
-            dt_us = max((t.t_end_ns - t.t_begin_ns) / 1000.0, 0.5)
-            prog = max(int(t.settled) - prev, 0)
-            prev = int(t.settled)
-            Xs.append(list(t.features))
-            As.append(int(t.action))
-            Ys.append(math.log2(1.0 + prog / dt_us))
+    for r in rs:
+        T, feat = {}, None
+        for a in range(pg.PG_NUM_ACTIONS):
+            script = np.array([base_a] * r + [a] * hold, dtype=np.uint8)
+            buf = (pg.RoundTrace * (r + 1))()
+            cfg = pg.default_config(schedule=pg.PG_SCHED_SCRIPT, script_len=len(script),
+                                    trace_cap=r + 1)
+            cfg.script = script.ctypes.data
+            cfg.trace_out = buf
+            ts = []
+            for _ in range(reps):
+                out = G.bfs(src, cfg=cfg, stats=st)
+                ts.append(st.kernel_ms)
+            if not torch.equal(out, ref):
+                raise RuntimeError("a schedule changed the distances")
+            T[a] = min(ts)
+            if st.rounds > r:
+                feat = list(buf[r].features)
+        if feat is None:
+            continue
+        best = min(T.values())
+        for a, t in T.items():
+            Xs.append(feat)
+            As.append(a)
+            Ys.append(-math.log2(t / best))
     return (np.asarray(Xs, np.float32), np.asarray(As, np.uint32), np.asarray(Ys, np.float32))
 
 
@@ -127,7 +141,7 @@ def train(X, A, Y, epochs=60, batch=4096, lr=3e-3, seed=0, log=print):
             t += 1
             pg.mlp_adam(P, grad, m, v, t, lr=lr)
             tot += float(loss.item()) * len(idx)
-        if ep % 10 == 0 or ep == epochs - 1:
+        if ep % 50 == 0 or ep == epochs - 1:
             log(f"epoch {ep:3d}  loss {tot / N:.4f}")
     return P.cpu().numpy(), mu, sd
 
@@ -154,9 +168,11 @@ def main():
     ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)),
                                                   "schedule_mlp.f32"))
     ap.add_argument("--quick", action="store_true")
-    ap.add_argument("--runs", type=int, default=4)
-    ap.add_argument("--epochs", type=int, default=60)
+    ap.add_argument("--sources", type=int, default=2)
+    ap.add_argument("--points", type=int, default=10)
+    ap.add_argument("--epochs", type=int, default=400)
     ap.add_argument("--log", default=None)
+    ap.add_argument("--eval", action="store_true", help="compare with fixed tau on held-out graphs")
     args = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
@@ -172,16 +188,27 @@ def main():
     for name, make in training_graphs(args.quick):
         g = make()
         G = pg.Graph.from_graphgen(g)
-        for si, src in enumerate(gg.pick_sources(g, 2, 7)):
-            X, A, Y = collect(G, int(src), seeds=[1000 * si + r for r in range(args.runs)])
+        for src in gg.pick_sources(g, args.sources, 7):
+            X, A, Y = collect(G, int(src), points=args.points)
             Xs.append(X); As.append(A); Ys.append(Y)
-            log(f"{name} src={int(src)} rounds={len(Y)}")
+            best = [int(np.argmax(Y[i:i + 8])) for i in range(0, len(Y), 8)]
+            log(f"{name} src={int(src)} states={len(Y) // 8} best actions={best}")
         G.free()
     X, A, Y = np.concatenate(Xs), np.concatenate(As), np.concatenate(Ys)
     log(f"samples {len(Y)}  collected in {time.time() - t0:.1f}s")
-    W, mu, sd = train(X, A, Y, epochs=args.epochs, log=log)
+    W, mu, sd = train(X, A, Y, epochs=args.epochs, batch=256, log=log)
     W.astype(np.float32).tofile(args.out)
     log(f"weights -> {args.out}")
+    if args.eval:
+        for name, make in (("knn_2m_k5_heldout", lambda: gg.knn(2_000_000, 5, 901)),
+                           ("knn_2m_k3_heldout", lambda: gg.knn(2_000_000, 3, 902)),
+                           ("grid_1000x1000", lambda: gg.grid(1000, 1000)),
+                           ("rmat_18_heldout", lambda: gg.rmat(18, 16, 903))):
+            g = make()
+            G = pg.Graph.from_graphgen(g)
+            res = evaluate(G, 0, W)
+            log(f"eval {name}: " + "  ".join(f"{k}={v['ms']:.2f}ms/{v['rounds']}r" for k, v in res.items()))
+            G.free()
     if args.log:
         with open(args.log, "w") as f:
             json.dump({"lines": lines, "samples": int(len(Y)), "target_mean": mu, "target_std": sd}, f)
