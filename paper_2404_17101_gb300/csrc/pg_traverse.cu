@@ -164,22 +164,21 @@ __device__ void push_global(const TravArgs &A, const Round &R, const uint32_t (&
                             const uint32_t (&nd)[kU], const bool (&go)[kU], int lane,
                             Counters &C) {
     bool keep[kU];
-    uint32_t deg[kU];
+    uint32_t deg[kU], prev[kU];
     const bool want_deg = A.need_deg || A.hubs_possible;
+    // all tag exchanges in flight before any result is compared
 #pragma unroll
     for (int u = 0; u < kU; u++) {
-        keep[u] = false;
         deg[u] = 0;
-        if (go[u]) {
-            if (R.dedupe) {
-                const uint32_t w = kReach ? (ent[u] & 0x7FFFFFFFu) : ent[u];
-                const uint32_t key = w + ((kReach && (ent[u] >> 31)) ? A.G.n : 0u);
-                keep[u] = atomicExch(&A.stamp[key], R.tag) != R.tag;
-            } else {
-                keep[u] = true;
-            }
+        prev[u] = 0;
+        if (go[u] && R.dedupe) {
+            const uint32_t w = kReach ? (ent[u] & 0x7FFFFFFFu) : ent[u];
+            const uint32_t key = w + ((kReach && (ent[u] >> 31)) ? A.G.n : 0u);
+            prev[u] = atomicExch(&A.stamp[key], R.tag);
         }
     }
+#pragma unroll
+    for (int u = 0; u < kU; u++) keep[u] = go[u] && (!R.dedupe || prev[u] != R.tag);
     if (want_deg) {
 #pragma unroll
         for (int u = 0; u < kU; u++) {
@@ -315,16 +314,21 @@ __device__ __forceinline__ unsigned long long load_prop(const TravArgs &A, uint3
     return d == PG_INF ? (unsigned long long)PG_INF : (unsigned long long)(d + 1);
 }
 
-// Relax arc (.., w) with propagated value p; true if w improved.
+// Relax arc (.., w) with propagated value p, in two halves so that a
+// warp issues all of its atomics before it waits for any result:
+// relax_issue returns the old value (a "no improvement" value when !ok),
+// improved() compares.
 template <bool kReach>
-__device__ __forceinline__ bool relax(const TravArgs &A, uint32_t w, uint32_t dir,
-                                     unsigned long long p) {
-    if (kReach) {
-        const unsigned long long old = atomicOr((dir ? A.mask1 : A.mask0) + w, p);
-        return (p & ~old) != 0ull;
-    }
-    const uint32_t nd = (uint32_t)p;
-    return nd < atomicMin(A.dist + w, nd);
+__device__ __forceinline__ unsigned long long relax_issue(const TravArgs &A, uint32_t w,
+                                                          uint32_t dir, unsigned long long p,
+                                                          bool ok) {
+    if (kReach) return ok ? atomicOr((dir ? A.mask1 : A.mask0) + w, p) : ~0ull;
+    return ok ? (unsigned long long)atomicMin(A.dist + w, (uint32_t)p) : 0ull;
+}
+template <bool kReach>
+__device__ __forceinline__ bool improved(unsigned long long p, unsigned long long old) {
+    if (kReach) return (p & ~old) != 0ull;
+    return (uint32_t)p < (uint32_t)old;
 }
 
 // Local eligibility of a child with aux value `caux` (BFS: its distance,
@@ -390,13 +394,16 @@ __device__ void expand_wave(const TravArgs &A, const Round &R, const WarpSm &S, 
     const bool row_lane = use_row && valid && !dead && !is_long;
     if (__any_sync(kFull, row_lane)) {
         bool imp[kMaxW];
+        unsigned long long old[kMaxW];
         uint32_t nvalid = 0;
 #pragma unroll
         for (int j = 0; j < (int)kMaxW; j++) {
             const bool ok = row_lane && (uint32_t)j < W && row[j] < 0x80000000u;
             nvalid += ok ? 1u : 0u;
-            imp[j] = ok && relax<kReach>(A, row[j], dir, prop);
+            old[j] = relax_issue<kReach>(A, row[j], dir, prop, ok);
         }
+#pragma unroll
+        for (int j = 0; j < (int)kMaxW; j++) imp[j] = improved<kReach>(prop, old[j]);
         if (row_lane) { C.expansions++; C.exp_verts++; C.exp_edges += nvalid; }
         const uint32_t wmax = max(A.ellw0, A.ellw1);
 #pragma unroll
@@ -446,8 +453,11 @@ __device__ void expand_wave(const TravArgs &A, const Round &R, const WarpSm &S, 
 #endif
             }
         }
+        unsigned long long old[kU];
 #pragma unroll
-        for (int u = 0; u < kU; u++) imp[u] = ok[u] && relax<kReach>(A, w[u], wd[u], pv[u]);
+        for (int u = 0; u < kU; u++) old[u] = relax_issue<kReach>(A, w[u], wd[u], pv[u], ok[u]);
+#pragma unroll
+        for (int u = 0; u < kU; u++) imp[u] = ok[u] && improved<kReach>(pv[u], old[u]);
 #pragma unroll
         for (int u = 0; u < kU; u++)
             stage<kReach>(A, R, S, T, imp[u], kReach ? (w[u] | (wd[u] << 31)) : w[u], ca[u],
@@ -548,8 +558,11 @@ __device__ void hub_edges(const TravArgs &A, const Round &R, const WarpSm &S, in
                     }
                 }
             }
+            unsigned long long old[kU];
 #pragma unroll
-            for (int u = 0; u < kU; u++) go[u] = go[u] && relax<kReach>(A, w[u], wd[u], pv[u]);
+            for (int u = 0; u < kU; u++) old[u] = relax_issue<kReach>(A, w[u], wd[u], pv[u], go[u]);
+#pragma unroll
+            for (int u = 0; u < kU; u++) go[u] = go[u] && improved<kReach>(pv[u], old[u]);
 #pragma unroll
             for (int u = 0; u < kU; u++)
                 stage<kReach>(A, R, S, T, go[u], kReach ? (w[u] | (wd[u] << 31)) : w[u],
