@@ -245,7 +245,7 @@ def main():
 
     fac, src, desc = WORKLOADS[args.workload]
     g = getattr(gg, fac)()
-    G = pg.Graph.from_graphgen(g)
+    G = pg.Graph.from_graphgen(g, ell=True)
     out = torch.empty(g.n, dtype=torch.int32, device="cuda")
 
     # --- forms: the plain fixed-tau traversal (library defaults), the same
@@ -338,7 +338,7 @@ def main():
             t0 = time.perf_counter()
             h = ctypes.c_void_p()
             pg._check(lib.pg_graph_upload(ctypes.c_void_p(off_h.data_ptr()),
-                                          ctypes.c_void_p(idx_h.data_ptr()), g.n, g.m, 0,
+                                          ctypes.c_void_p(idx_h.data_ptr()), g.n, g.m, pg.PG_ELL,
                                           pg._stream_ptr(), ctypes.byref(h)))
             if head == "learned":
                 pg._check(lib.pg_set_schedule_weights(h, ctypes.c_void_p(w.ctypes.data), w.size))

@@ -57,6 +57,15 @@ typedef enum pg_status {
 #define PG_SCHED_RANDOM 2u  /* uniformly random action per round (trace collection) */
 #define PG_SCHED_SCRIPT 3u  /* per-round action read from cfg->script (tests) */
 
+/* local-search organisation (pg_config.vgc_mode), for rounds with tau > 1:
+ * PG_VGC_CTA: a CTA takes a share of the frontier and runs a level-by-level
+ *   local search of up to tau levels in shared memory, all its warps
+ *   splitting each level (levels separated by a CTA barrier);
+ * PG_VGC_WARP: every warp runs its own FIFO local search from a chunk of
+ *   `chunk` frontier entries. */
+#define PG_VGC_CTA 0u
+#define PG_VGC_WARP 1u
+
 /* direction policy for PG_SCHED_FIXED */
 #define PG_DIR_PUSH 0u
 #define PG_DIR_AUTO 1u
@@ -106,6 +115,8 @@ typedef struct pg_config {
     uint32_t script_len;        /* entries in script */
     uint32_t trace_cap;         /* records available in trace_out */
     uint32_t test_stall_block;  /* fault injection: this CTA never arrives at the grid barrier; 0xFFFFFFFF = off */
+    uint32_t vgc_mode;          /* local search for tau > 1: PG_VGC_CTA (default) or PG_VGC_WARP */
+    uint32_t cta_queue;         /* PG_VGC_CTA: vertices per level a CTA keeps locally (64..8192); 0 = 2048 */
     uint32_t reserved;
     const uint8_t *script;      /* host: action per round for PG_SCHED_SCRIPT (round i uses script[i % len]) */
     pg_round_trace *trace_out;  /* host buffer for per-round records, or NULL */

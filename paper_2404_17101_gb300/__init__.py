@@ -28,6 +28,7 @@ PG_DIRECTED, PG_BUILD_TRANSPOSE, PG_SKIP_VALIDATE, PG_ELL = 1, 2, 4, 8
 PG_FWD, PG_BWD = 1, 2
 PG_SCHED_FIXED, PG_SCHED_LEARNED, PG_SCHED_RANDOM, PG_SCHED_SCRIPT = 0, 1, 2, 3
 PG_DIR_PUSH, PG_DIR_AUTO = 0, 1
+PG_VGC_CTA, PG_VGC_WARP = 0, 1
 PG_NUM_ACTIONS, PG_ACTION_PULL = 8, 7
 PG_MLP_NPARAMS = 1512
 INF = 0xFFFFFFFF
@@ -63,7 +64,8 @@ class Config(ctypes.Structure):
                 ("hub_degree", ctypes.c_uint32), ("timeout_ms", ctypes.c_uint32),
                 ("max_rounds", ctypes.c_uint32), ("seed", ctypes.c_uint32),
                 ("script_len", ctypes.c_uint32), ("trace_cap", ctypes.c_uint32),
-                ("test_stall_block", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("test_stall_block", ctypes.c_uint32), ("vgc_mode", ctypes.c_uint32),
+                ("cta_queue", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
                 ("script", ctypes.c_void_p), ("trace_out", ctypes.POINTER(RoundTrace)),
                 ("ref_dist", ctypes.c_void_p)]
 

@@ -193,6 +193,8 @@ struct PgLaunch {
     const float *weights;        // device
     uint32_t epoch;
     uint32_t allow_pull;
+    uint32_t vgc;        // PG_VGC_CTA / PG_VGC_WARP
+    uint32_t cta_queue;  // CTA level-buffer capacity
 };
 
 pg_status pg_resolve_config(pg_graph *g, const pg_config *cfg, PgLaunch *L);

@@ -108,6 +108,27 @@ struct Task {
     uint32_t qhead, qtail;   // local FIFO cursors (warp-uniform)
     uint32_t budget;         // local enqueues left
     uint32_t nsp;            // staged spills
+    // CTA level-synchronous local search: when cta_n is set, local children
+    // go to the CTA's next-level buffer instead of the warp FIFO
+    uint32_t *cta_ent, *cta_aux;
+    unsigned *cta_n;
+    uint32_t cta_cap;
+};
+
+__device__ __forceinline__ void task_init(Task &T, uint32_t budget) {
+    T.qhead = T.qtail = 0;
+    T.nsp = 0;
+    T.budget = budget;
+    T.cta_ent = T.cta_aux = nullptr;
+    T.cta_n = nullptr;
+    T.cta_cap = 0;
+}
+
+// Shared-memory level buffers of the CTA local search.
+struct CtaSm {
+    uint32_t *ent[2], *aux[2];
+    unsigned *n;      // [2] level sizes
+    unsigned *task;   // grabbed task base
 };
 
 struct Counters {
@@ -279,7 +300,17 @@ __device__ __forceinline__ void stage(const TravArgs &A, const Round &R, const W
     const bool want = imp && eligible;
     const unsigned bl = __ballot_sync(kFull, want);
     bool to_local = false;
-    if (bl) {
+    if (bl && T.cta_n != nullptr) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(T.cta_n, (unsigned)__popc(bl));
+        base = __shfl_sync(kFull, base, 0);
+        const uint32_t p = base + __popc(bl & lt);
+        to_local = want && p < T.cta_cap;
+        if (to_local) {
+            T.cta_ent[p] = ent;
+            T.cta_aux[p] = aux;
+        }
+    } else if (bl) {
         const uint32_t room = min(A.L.qcap - (T.qtail - T.qhead), T.budget);
         const uint32_t nl = min((uint32_t)__popc(bl), room);
         const uint32_t rank = __popc(bl & lt);
@@ -471,9 +502,7 @@ template <bool kReach>
 __device__ void run_task(const TravArgs &A, const Round &R, const WarpSm &S, uint32_t entry,
                          uint32_t c, int lane, Counters &C) {
     Task T;
-    T.qhead = T.qtail = 0;
-    T.nsp = 0;
-    T.budget = (R.tau > 1u) ? c * R.tau * 8u : 0u;
+    task_init(T, (R.tau > 1u) ? c * R.tau * 8u : 0u);
     uint32_t aux = 0;
     bool from_bag = true;
     for (;;) {
@@ -493,6 +522,64 @@ __device__ void run_task(const TravArgs &A, const Round &R, const WarpSm &S, uin
     flush_spill<kReach>(A, R, S, T, lane, C);
 }
 
+// CTA-cooperative local search for one round (tau > 1): the CTA takes a
+// share of the frontier (static first, then grabbed), and runs it level by
+// level for up to tau levels: all warps split each level, children inside
+// the window go to the CTA's next-level buffer in shared memory, the rest
+// (and any overflow) spill to the next bag.  Levels are separated by a CTA
+// barrier, so the CTA's local search is itself breadth-first.
+template <bool kReach>
+__device__ void cta_round(const TravArgs &A, const Round &R, const WarpSm &S, const CtaSm &Q,
+                          int lane, int wib, int nwib, Counters &C) {
+    const uint32_t nb = gridDim.x;
+    const uint32_t QC = A.L.cta_queue;
+    uint32_t cc = (R.F + nb - 1) / nb;
+    cc = max(1u, min(cc, QC / 2));
+    const uint32_t span = nb * cc;
+    Task T;
+    task_init(T, 0);
+    for (uint32_t base = blockIdx.x * cc;;) {
+        if (base >= R.F) break;
+        const uint32_t c = min(cc, R.F - base);
+        for (uint32_t i = threadIdx.x; i < c; i += blockDim.x) {
+            uint32_t e = __ldcg(A.bag + (size_t)R.cur * A.cap + base + i);
+            e = PG_DBG_ENTRY(A, e, 7u, kReach);
+            Q.ent[0][i] = e;
+            Q.aux[0][i] = 0u;
+        }
+        if (threadIdx.x == 0) {
+            Q.n[0] = c;
+            Q.n[1] = 0;
+        }
+        __syncthreads();
+        for (uint32_t h = 0;; h++) {
+            const uint32_t cl = h & 1u, nl = cl ^ 1u;
+            const uint32_t ncur = min(Q.n[cl], QC);
+            if (ncur == 0) break;
+            T.cta_ent = Q.ent[nl];
+            T.cta_aux = Q.aux[nl];
+            T.cta_n = &Q.n[nl];
+            T.cta_cap = QC;
+            for (uint32_t w0 = (uint32_t)wib * 32u; w0 < ncur; w0 += (uint32_t)nwib * 32u) {
+                const uint32_t i = w0 + lane;
+                const uint32_t e = (i < ncur) ? Q.ent[cl][i] : PG_NONE;
+                const uint32_t ax = (i < ncur) ? Q.aux[cl][i] : 0u;
+                expand_wave<kReach>(A, R, S, T, e, ax, h == 0, lane, C);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) Q.n[cl] = 0;
+            __syncthreads();
+        }
+        T.cta_n = nullptr;
+        flush_spill<kReach>(A, R, S, T, lane, C);
+        if (R.F <= span) break;
+        if (threadIdx.x == 0) *Q.task = span + atomicAdd(&R.sc->head, cc);
+        __syncthreads();
+        base = *Q.task;
+        __syncthreads();
+    }
+}
+
 // Edges of listed hubs, dealt in chunks of `hch` edges (hch <= hub_degree, so
 // a chunk touches at most two hubs).  Improvements go to the next bag.
 template <bool kReach>
@@ -505,9 +592,7 @@ __device__ void hub_edges(const TravArgs &A, const Round &R, const WarpSm &S, in
     const uint32_t hch = min(1024u, A.L.hub_degree);
     const PgHub *H = A.hubs + (size_t)R.cur * A.hcap;
     Task T;
-    T.qhead = T.qtail = 0;
-    T.nsp = 0;
-    T.budget = 0;
+    task_init(T, 0);
     for (;;) {
         uint32_t a = 0;
         if (lane == 0) a = atomicAdd(&R.sc->hub_cursor, hch);
@@ -580,9 +665,7 @@ __device__ void pull_round(const TravArgs &A, const Round &R, const WarpSm &S, u
     const uint32_t n = A.G.n;
     const uint32_t target = Lvl + 1u;
     Task T;
-    T.qhead = T.qtail = 0;
-    T.nsp = 0;
-    T.budget = 0;
+    task_init(T, 0);
     const uint32_t W = A.ellw1;
     for (uint32_t base = gwarp * 32u; base < n; base += nwarps * 32u) {
         const uint32_t v = base + lane;
@@ -720,6 +803,16 @@ __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
     S.spa = S.sp + kSpillCap;
     S.lq = S.spa + kSpillCap;
     S.lqa = S.lq + A.L.qcap;
+    CtaSm Q;
+    {
+        uint32_t *cta = s_u32 + (size_t)nwib * per_warp;
+        Q.ent[0] = cta;
+        Q.ent[1] = cta + A.L.cta_queue;
+        Q.aux[0] = cta + 2u * A.L.cta_queue;
+        Q.aux[1] = cta + 3u * A.L.cta_queue;
+        Q.n = cta + 4u * A.L.cta_queue;
+        Q.task = Q.n + 2;
+    }
 
     if (A.L.schedule == PG_SCHED_LEARNED)
         for (int i = threadIdx.x; i < (int)PG_MLP_NPARAMS; i += blockDim.x) s_w[i] = A.L.weights[i];
@@ -894,6 +987,9 @@ __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
         if (pull) {
             pull_round(A, R, S, Lvl, lane, gwarp, nwarps, C);
             pull_rounds++;
+        } else if (R.tau > 1u && A.L.vgc == PG_VGC_CTA) {
+            cta_round<kReach>(A, R, S, Q, lane, wib, nwib, C);
+            hub_edges<kReach>(A, R, S, lane, C);
         } else {
             // first task of every warp assigned statically, the rest grabbed
             const uint32_t span = nwarps * A.L.chunk;
@@ -966,15 +1062,16 @@ __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
     }
 }
 
-size_t traverse_smem(uint32_t threads, uint32_t qcap) {
+size_t traverse_smem(uint32_t threads, uint32_t qcap, uint32_t cta_queue) {
     const uint32_t nw = threads / 32;
-    return 6144 + (size_t)nw * 256 + (size_t)nw * (4u * 32u + 2u * kSpillCap + 2u * qcap) * 4u;
+    return 6144 + (size_t)nw * 256 + (size_t)nw * (4u * 32u + 2u * kSpillCap + 2u * qcap) * 4u +
+           (size_t)(4u * cta_queue + 4u) * 4u;
 }
 
 template <bool kReach>
 pg_status launch_impl(pg_graph *g, PgLaunch &L, TravArgs &A, cudaStream_t s) {
     auto kern = pg_traverse_kernel<kReach>;
-    const size_t smem = traverse_smem(L.threads, L.qcap);
+    const size_t smem = traverse_smem(L.threads, L.qcap, L.cta_queue);
     int maxopt = 0;
     PG_CK(cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device));
     if (smem > (size_t)maxopt)
@@ -1023,7 +1120,7 @@ pg_status pg_launch_bfs_raw(const PgRawBfs &w, PgLaunch &L, cudaStream_t s) {
     A.need_deg = 0;
     A.hubs_possible = 0;
     auto kern = pg_traverse_kernel<false>;
-    const size_t smem = traverse_smem(L.threads, L.qcap);
+    const size_t smem = traverse_smem(L.threads, L.qcap, L.cta_queue);
     int maxopt = 0;
     PG_CK(cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, w.device));
     if (smem > (size_t)maxopt)

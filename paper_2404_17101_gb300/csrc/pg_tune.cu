@@ -2,6 +2,8 @@
 //
 // The paper leaves tau tunable (Sec. 2.1); on the GPU the local-queue size,
 // the task chunk, the threads per CTA and the CTAs per SM matter as much.
+// Knobs: local-search organisation (CTA / warp), tau, task chunk, warp
+// queue, CTA queue, threads per CTA, CTAs per SM.
 // Coordinate descent: for each knob in turn, time every candidate value
 // with the others fixed at the best so far (median of `trials` CUDA-event
 // timed runs) and keep the fastest.  Outputs go to scratch buffers that the
@@ -70,29 +72,35 @@ extern "C" pg_status pg_autotune(pg_graph *g, uint32_t kind, const uint32_t *sou
     };
     // warm-up and baseline
     st = measure(best, &best_ms);
+    const uint32_t modes[] = {PG_VGC_CTA, PG_VGC_WARP};
     const uint32_t taus[] = {1, 2, 4, 8, 16, 32, 64};
     const uint32_t chunks[] = {1, 2, 4, 8, 32};
     const uint32_t queues[] = {128, 512, 2048};
+    const uint32_t ctaq[] = {1024, 2048, 4096};
     const uint32_t threads[] = {256, 512};
     const uint32_t bps[] = {1, 2, 3, 4};
-    for (int knob = 0; knob < 5 && !st; knob++) {
+    for (int knob = 0; knob < 7 && !st; knob++) {
         const uint32_t *vals;
         int nv;
         switch (knob) {
-            case 0: vals = taus; nv = 7; break;
-            case 1: vals = chunks; nv = 5; break;
-            case 2: vals = queues; nv = 3; break;
-            case 3: vals = threads; nv = 2; break;
+            case 0: vals = modes; nv = 2; break;
+            case 1: vals = taus; nv = 7; break;
+            case 2: vals = chunks; nv = 5; break;
+            case 3: vals = queues; nv = 3; break;
+            case 4: vals = ctaq; nv = 3; break;
+            case 5: vals = threads; nv = 2; break;
             default: vals = bps; nv = 4; break;
         }
         pg_config cur = best;
         for (int i = 0; i < nv && !st; i++) {
             pg_config c = best;
             switch (knob) {
-                case 0: c.tau = vals[i]; break;
-                case 1: c.chunk = vals[i]; break;
-                case 2: c.local_queue = vals[i]; break;
-                case 3: c.threads_per_block = vals[i]; break;
+                case 0: c.vgc_mode = vals[i]; break;
+                case 1: c.tau = vals[i]; break;
+                case 2: c.chunk = vals[i]; break;
+                case 3: c.local_queue = vals[i]; break;
+                case 4: c.cta_queue = vals[i]; break;
+                case 5: c.threads_per_block = vals[i]; break;
                 default: c.blocks_per_sm = vals[i]; break;
             }
             float ms = 0;
@@ -108,6 +116,8 @@ extern "C" pg_status pg_autotune(pg_graph *g, uint32_t kind, const uint32_t *sou
     cudaFree(out0);
     cudaFree(out1);
     if (st) return st;
+    cfg->vgc_mode = best.vgc_mode;
+    cfg->cta_queue = best.cta_queue;
     cfg->tau = best.tau;
     cfg->chunk = best.chunk;
     cfg->local_queue = best.local_queue;
