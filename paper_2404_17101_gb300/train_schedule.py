@@ -68,7 +68,7 @@ def training_graphs(quick: bool):
     return fams
 
 
-def collect(G, src, base_tau=8, points=10, reps=2, hold=80_000):
+def collect(G, src, base_tau=16, points=10, reps=2, hold=80_000):
     """Rollout samples (features of round r, action, label) for one source."""
     import torch
     base_a = int(round(math.log2(base_tau)))
@@ -187,7 +187,7 @@ def main():
     t0 = time.time()
     for name, make in training_graphs(args.quick):
         g = make()
-        G = pg.Graph.from_graphgen(g)
+        G = pg.Graph.from_graphgen(g, ell=True)
         for src in gg.pick_sources(g, args.sources, 7):
             X, A, Y = collect(G, int(src), points=args.points)
             Xs.append(X); As.append(A); Ys.append(Y)
@@ -205,7 +205,7 @@ def main():
                            ("grid_1000x1000", lambda: gg.grid(1000, 1000)),
                            ("rmat_18_heldout", lambda: gg.rmat(18, 16, 903))):
             g = make()
-            G = pg.Graph.from_graphgen(g)
+            G = pg.Graph.from_graphgen(g, ell=True)
             res = evaluate(G, 0, W)
             log(f"eval {name}: " + "  ".join(f"{k}={v['ms']:.2f}ms/{v['rounds']}r" for k, v in res.items()))
             G.free()
