@@ -252,6 +252,17 @@ class Graph:
                                        ctypes.byref(b), _stream_ptr(stream)))
         return a.value, b.value
 
+    def set_transpose(self, t_offsets, t_indices, stream=None):
+        """Replace the reversed CSR (host numpy arrays or CUDA tensors, uint32)."""
+        ptrs = []
+        for a in (t_offsets, t_indices):
+            if isinstance(a, np.ndarray):
+                a = np.ascontiguousarray(a, dtype=np.uint32)
+                ptrs.append((a, ctypes.c_void_p(a.ctypes.data)))
+            else:
+                ptrs.append((a, ctypes.c_void_p(a.data_ptr())))
+        _check(load().pg_graph_set_transpose(self._h, ptrs[0][1], ptrs[1][1], _stream_ptr(stream)))
+
     def set_schedule_weights(self, w):
         a = np.ascontiguousarray(w, dtype=np.float32)
         _check(load().pg_set_schedule_weights(self._h, ctypes.c_void_p(a.ctypes.data), a.size))

@@ -240,7 +240,7 @@ __global__ void k_sort_rows(const uint32_t *off, uint32_t *idx, uint32_t n) {
     }
 }
 
-static pg_status exclusive_scan(const uint32_t *in, uint32_t *out, uint32_t len, cudaStream_t s) {
+pg_status pg_exclusive_scan(const uint32_t *in, uint32_t *out, uint32_t len, cudaStream_t s) {
     const uint32_t nb = (len + kScanItems - 1) / kScanItems;
     uint32_t *sums = nullptr;
     PG_CK(cudaMallocAsync(&sums, (size_t)(nb ? nb : 1) * sizeof(uint32_t), s));
@@ -261,7 +261,7 @@ static pg_status build_transpose(pg_graph *g, cudaStream_t s) {
     if (m) k_count_in<<<grid, 256, 0, s>>>(g->d_idx, m, cnt);
     PG_CK(cudaMallocAsync(&g->d_toff, ((size_t)n + 1) * sizeof(uint32_t), s));
     PG_CK(cudaMallocAsync(&g->d_tidx, (size_t)(m ? m : 1) * sizeof(uint32_t), s));
-    pg_status st = exclusive_scan(cnt, g->d_toff, n + 1, s);
+    pg_status st = pg_exclusive_scan(cnt, g->d_toff, n + 1, s);
     if (st) return st;
     PG_CK(cudaMemcpyAsync(cnt, g->d_toff, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     if (m) {
@@ -395,7 +395,6 @@ static void release(pg_graph *g) {
     cudaFree(g->d_weights);
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
-    extern void pg_msbfs_release(pg_graph *);
     pg_msbfs_release(g);
     delete g;
 }
@@ -497,6 +496,7 @@ extern "C" pg_status pg_graph_set_transpose(pg_graph *g, const uint32_t *t_offse
     if (st) { cudaFree(toff); cudaFree(tidx); return st; }
     if (!g->transpose_is_self) { cudaFree(g->d_toff); cudaFree(g->d_tidx); }
     if (g->d_ell[1] && g->d_ell[1] != g->d_ell[0]) cudaFree(g->d_ell[1]);
+    pg_msbfs_release(g);  // its in-edge chunk list refers to the old transpose
     g->d_ell[1] = nullptr;
     g->ellw[1] = 0;
     g->d_toff = toff;

@@ -84,6 +84,11 @@ __device__ __forceinline__ unsigned long long pg_ldcg64(const unsigned long long
     return __ldcg(p);
 }
 
+// Fire-and-forget fetch of the line holding p into this SM's L1 (and L2).
+__device__ __forceinline__ void pg_prefetch_l1(const void *p) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ unsigned pg_lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -149,6 +154,7 @@ int pg_device_sms(int dev);
     } while (0)
 
 struct PgMsbfsWork;  // batched BFS buffers (pg_msbfs.cu)
+void pg_msbfs_release(pg_graph *g);  // frees them; rebuilt on the next batched call
 
 struct pg_graph {
     int device;
@@ -199,6 +205,8 @@ struct PgLaunch {
 
 pg_status pg_resolve_config(pg_graph *g, const pg_config *cfg, PgLaunch *L);
 pg_status pg_stage(pg_graph *g, size_t bytes, void **dev);
+// out[i] = in[0] + ... + in[i-1] for i < len (device arrays, stream-ordered)
+pg_status pg_exclusive_scan(const uint32_t *in, uint32_t *out, uint32_t len, cudaStream_t s);
 bool pg_is_device_ptr(const void *p);
 pg_status pg_ensure_trace(pg_graph *g, const pg_config *cfg, PgLaunch *L, cudaStream_t s);
 pg_status pg_finish_call(pg_graph *g, const PgLaunch &L, const pg_config *cfg,

@@ -8,16 +8,33 @@
 // soon as every missing bit is found), chosen with the direction-
 // optimisation test of [Beamer12] (Sec. 2.2).  A bit that first appears at a
 // vertex in round L gives that source's hop distance L + 1 (Sec. 2.2).
+//
+// High-degree splitting (the load balance of Sec. 2.1's small-task
+// discussion): a vertex with at least kHeavy edges in a direction is never
+// expanded by one thread or one warp alone.  Its list is cut into chunks of
+// at most kChunk edges, listed once per graph, and any warp takes a chunk:
+// top-down ORs the vertex's bits into the chunk's targets, bottom-up ORs the
+// chunk's visit words (32 at a time, stopping once every missing bit is
+// found) and merges them into next[w] with one atomicOr.
 #include "pg_internal.cuh"
+
+namespace {
+constexpr uint32_t kHeavy = 32;    // edges: below, one thread (bottom-up) / one lane (top-down)
+constexpr uint32_t kChunk = 1024;  // edges per chunk of a heavy vertex
+}  // namespace
 
 struct PgMsbfsWork {
     unsigned long long *seen, *visit, *next;
     uint32_t n;
+    uint2 *chunks[2];     // (vertex, first edge) per chunk: out-lists, in-lists
+    uint32_t nchunks[2];
 };
 
 void pg_msbfs_release(pg_graph *g) {
     if (g && g->msbfs) {
         cudaFree(g->msbfs->seen);
+        cudaFree(g->msbfs->chunks[0]);
+        if (g->msbfs->chunks[1] != g->msbfs->chunks[0]) cudaFree(g->msbfs->chunks[1]);
         delete g->msbfs;
         g->msbfs = nullptr;
     }
@@ -27,8 +44,33 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
+// chunks of each heavy vertex: cnt[v] = ceil(deg / kChunk) when deg >= kHeavy
+__global__ void k_chunk_count(const uint32_t *off, uint32_t n, uint32_t *cnt) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += stride) {
+        uint32_t c = 0;
+        if (v < n) {
+            const uint32_t d = off[v + 1] - off[v];
+            c = d >= kHeavy ? (d + kChunk - 1) / kChunk : 0u;
+        }
+        cnt[v] = c;
+    }
+}
+
+__global__ void k_chunk_fill(const uint32_t *off, uint32_t n, const uint32_t *pos, uint2 *chunks) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const uint32_t b = off[v], d = off[v + 1] - b;
+        if (d < kHeavy) continue;
+        const uint32_t c = (d + kChunk - 1) / kChunk;
+        for (uint32_t i = 0; i < c; i++) chunks[pos[v] + i] = make_uint2(v, b + i * kChunk);
+    }
+}
+
 struct MsArgs {
     PgGraphDev G;
+    const uint2 *chunks_out, *chunks_in;
+    uint32_t nchunks_out, nchunks_in;
     PgCtrl *ctrl;
     unsigned long long *seen, *visit, *next;
     uint32_t *dist;       // k * n, source-major
@@ -121,16 +163,39 @@ __global__ void __launch_bounds__(512) pg_msbfs_kernel(const MsArgs A) {
         edges_seen += E;
         if (bottom_up) {
             pulls++;
+            // light vertices: one thread each, four gathers in flight
             for (uint32_t w = gtid; w < n; w += gthreads) {
                 const unsigned long long need = full & ~A.seen[w];
                 if (!need) continue;
-                unsigned long long acc = 0;
                 const uint32_t b = __ldg(A.G.toff + w), e = __ldg(A.G.toff + w + 1);
-                for (uint32_t q = b; q < e; q++) {
-                    acc |= __ldcg(A.visit + __ldg(A.G.tidx + q));
+                if (e - b >= kHeavy) continue;  // in the chunk list
+                unsigned long long acc = 0;
+                for (uint32_t q = b; q < e; q += 4) {
+                    uint32_t u[4];
+#pragma unroll
+                    for (int i = 0; i < 4; i++) u[i] = (q + i < e) ? __ldg(A.G.tidx + q + i) : PG_NONE;
+#pragma unroll
+                    for (int i = 0; i < 4; i++)
+                        if (u[i] != PG_NONE) acc |= __ldcg(A.visit + u[i]);
                     if ((acc & need) == need) break;
                 }
                 if (acc & need) A.next[w] = acc & need;
+            }
+            // heavy vertices: one warp per chunk of in-edges
+            for (uint32_t c = gwarp; c < A.nchunks_in; c += nwarps) {
+                const uint2 ch = A.chunks_in[c];
+                const uint32_t w = ch.x;
+                const unsigned long long need = full & ~__ldcg(A.seen + w);
+                if (!need) continue;
+                const uint32_t e = min(ch.y + kChunk, __ldg(A.G.toff + w + 1));
+                unsigned long long acc = 0;
+                for (uint32_t q = ch.y; q < e; q += 32u) {
+                    if (q + lane < e) acc |= __ldcg(A.visit + __ldg(A.G.tidx + q + lane));
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) acc |= __shfl_xor_sync(kFull, acc, o);
+                    if ((acc & need) == need) break;
+                }
+                if (lane == 0 && (acc & need)) atomicOr(A.next + w, acc & need);
             }
         } else {
             // top-down: warps take 32 consecutive vertices, expand the
@@ -144,6 +209,7 @@ __global__ void __launch_bounds__(512) pg_msbfs_kernel(const MsArgs A) {
                     if (bits) {
                         beg = __ldg(A.G.off + v);
                         deg = __ldg(A.G.off + v + 1) - beg;
+                        if (deg >= kHeavy) deg = 0;  // in the chunk list
                     }
                 }
                 uint32_t incl = deg;
@@ -168,6 +234,14 @@ __global__ void __launch_bounds__(512) pg_msbfs_kernel(const MsArgs A) {
                     atomicOr(A.next + w, s_bits[wib][o]);
                 }
                 __syncwarp();
+            }
+            // heavy frontier vertices: one warp per chunk of out-edges
+            for (uint32_t c = gwarp; c < A.nchunks_out; c += nwarps) {
+                const uint2 ch = A.chunks_out[c];
+                const unsigned long long bits = __ldcg(A.visit + ch.x);
+                if (!bits) continue;
+                const uint32_t e = min(ch.y + kChunk, __ldg(A.G.off + ch.x + 1));
+                for (uint32_t q = ch.y + lane; q < e; q += 32u) atomicOr(A.next + __ldg(A.G.idx + q), bits);
             }
         }
         if (!pg_grid_sync(ctrl, gridDim.x, gen, A.timeout_ns, &s_flag)) break;
@@ -220,6 +294,32 @@ __global__ void __launch_bounds__(512) pg_msbfs_kernel(const MsArgs A) {
 
 }  // namespace
 
+// The chunk list of one direction (built once per graph, on first use).
+static pg_status build_chunks(pg_graph *g, const uint32_t *off, uint2 **out, uint32_t *count,
+                              cudaStream_t s) {
+    const uint32_t n = g->n;
+    *out = nullptr;
+    *count = 0;
+    uint32_t *cnt = nullptr;
+    PG_CK(cudaMallocAsync(&cnt, ((size_t)n + 1) * 2 * sizeof(uint32_t), s));
+    uint32_t *pos = cnt + n + 1;
+    k_chunk_count<<<g->num_sms * 4, 256, 0, s>>>(off, n, cnt);
+    PG_CK(cudaGetLastError());
+    pg_status st = pg_exclusive_scan(cnt, pos, n + 1, s);
+    if (st) return st;
+    uint32_t total = 0;
+    PG_CK(cudaMemcpyAsync(&total, pos + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    PG_CK(cudaStreamSynchronize(s));
+    uint2 *ch = nullptr;
+    PG_CK(cudaMalloc(&ch, (size_t)(total ? total : 1) * sizeof(uint2)));
+    if (total) k_chunk_fill<<<g->num_sms * 4, 256, 0, s>>>(off, n, pos, ch);
+    PG_CK(cudaGetLastError());
+    PG_CK(cudaFreeAsync(cnt, s));
+    *out = ch;
+    *count = total;
+    return PG_OK;
+}
+
 pg_status pg_launch_msbfs(pg_graph *g, PgLaunch &L, const uint32_t *sources, uint32_t k,
                           uint32_t *dist, cudaStream_t s) {
     if (!g->msbfs) {
@@ -236,6 +336,19 @@ pg_status pg_launch_msbfs(pg_graph *g, PgLaunch &L, const uint32_t *sources, uin
         g->msbfs->visit = p + g->n;
         g->msbfs->next = p + 2 * (size_t)g->n;
         g->msbfs->n = g->n;
+        const bool self = g->transpose_is_self || !g->d_toff;
+        for (int d = 0; d < (self ? 1 : 2); d++) {
+            pg_status st = build_chunks(g, d ? g->d_toff : g->d_off, &g->msbfs->chunks[d],
+                                        &g->msbfs->nchunks[d], s);
+            if (st) {
+                pg_msbfs_release(g);
+                return st;
+            }
+        }
+        if (self) {
+            g->msbfs->chunks[1] = g->msbfs->chunks[0];
+            g->msbfs->nchunks[1] = g->msbfs->nchunks[0];
+        }
     }
     MsArgs A;
     memset(&A, 0, sizeof(A));
@@ -245,6 +358,10 @@ pg_status pg_launch_msbfs(pg_graph *g, PgLaunch &L, const uint32_t *sources, uin
     A.G.tidx = g->d_tidx ? g->d_tidx : g->d_idx;
     A.G.n = g->n;
     A.G.m = g->m;
+    A.chunks_out = g->msbfs->chunks[0];
+    A.nchunks_out = g->msbfs->nchunks[0];
+    A.chunks_in = g->msbfs->chunks[1];
+    A.nchunks_in = g->has_transpose ? g->msbfs->nchunks[1] : 0u;
     A.ctrl = g->d_ctrl;
     A.seen = g->msbfs->seen;
     A.visit = g->msbfs->visit;

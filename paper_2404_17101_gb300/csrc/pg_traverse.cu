@@ -126,9 +126,9 @@ __device__ __forceinline__ void task_init(Task &T, uint32_t budget) {
 
 // Shared-memory level buffers of the CTA local search.
 struct CtaSm {
-    uint32_t *ent[2], *aux[2];
-    unsigned *n;      // [2] level sizes
-    unsigned *task;   // grabbed task base
+    uint32_t *ent[3], *aux[3];  // three level buffers, rotating
+    unsigned *n;                // [3] level sizes
+    unsigned *task;             // grabbed task base
 };
 
 struct Counters {
@@ -336,6 +336,68 @@ __device__ __forceinline__ void stage(const TravArgs &A, const Round &R, const W
     }
 }
 
+// Route a whole padded-row wave at once (CTA local search): one warp scan
+// and one shared-memory atomic reserve the lanes' local slots; the rest go
+// to the spill staging.  Children of one lane share eligibility (same
+// parent).  If the spills do not fit the staging even after a flush, they
+// are routed one slot at a time through stage().
+template <bool kReach>
+__device__ void stage_rows(const TravArgs &A, const Round &R, const WarpSm &S, Task &T,
+                           const bool (&imp)[kMaxW], const uint32_t (&row)[kMaxW], uint32_t dir,
+                           uint32_t caux, bool ok_local, uint32_t wmax, int lane, Counters &C) {
+    uint32_t mask = 0;
+#pragma unroll
+    for (int j = 0; j < (int)kMaxW; j++)
+        if (imp[j]) mask |= 1u << j;
+    const uint32_t cnt = __popc(mask);
+    const uint32_t want = ok_local ? cnt : 0u;
+    const uint32_t incl = warp_incl_scan(want, lane);
+    const uint32_t tot = __shfl_sync(kFull, incl, 31);
+    uint32_t base = 0;
+    if (lane == 0 && tot) base = atomicAdd(T.cta_n, tot);
+    base = __shfl_sync(kFull, base, 0);
+    const uint32_t p0 = base + incl - want;
+    const uint32_t nfit = (p0 < T.cta_cap) ? min(want, T.cta_cap - p0) : 0u;
+    const uint32_t nsl = cnt - nfit;
+    // inside the window nothing spills: skip the second scan
+    const bool any_sl = __any_sync(kFull, nsl != 0u);
+    const uint32_t sincl = any_sl ? warp_incl_scan(nsl, lane) : 0u;
+    const uint32_t stot = any_sl ? __shfl_sync(kFull, sincl, 31) : 0u;
+    if (stot && T.nsp + stot > kSpillCap) flush_spill<kReach>(A, R, S, T, lane, C);
+    const bool batch_spill = stot <= kSpillCap;
+    uint32_t k = 0, q = T.nsp + sincl - nsl;
+#pragma unroll
+    for (int j = 0; j < (int)kMaxW; j++) {
+        if ((mask >> j) & 1u) {
+            const uint32_t ent = kReach ? (row[j] | (dir << 31)) : row[j];
+            if (k < nfit) {
+                T.cta_ent[p0 + k] = ent;
+                T.cta_aux[p0 + k] = caux;
+            } else if (batch_spill) {
+                S.sp[q] = ent;
+                S.spa[q] = caux;
+                q++;
+            }
+            k++;
+        }
+    }
+    if (batch_spill) {
+        T.nsp += stot;
+        return;
+    }
+    // rare: more spills than the staging holds -- slot by slot
+    uint32_t seen = 0;
+#pragma unroll
+    for (int j = 0; j < (int)kMaxW; j++) {
+        const bool bit = (mask >> j) & 1u;
+        const bool sp = bit && seen >= nfit;
+        seen += bit ? 1u : 0u;
+        if ((uint32_t)j < wmax)
+            stage<kReach>(A, R, S, T, sp, kReach ? (row[j] | (dir << 31)) : row[j], caux, false,
+                          lane, C);
+    }
+}
+
 // Value a vertex propagates: BFS d + 1 (INF stays INF), REACH its mask.
 template <bool kReach>
 __device__ __forceinline__ unsigned long long load_prop(const TravArgs &A, uint32_t v,
@@ -388,7 +450,10 @@ __device__ void expand_wave(const TravArgs &A, const Round &R, const WarpSm &S, 
     for (int j = 0; j < (int)kMaxW; j++) row[j] = PG_NONE;
     bool use_row = false;
     if (valid) {
-        prop = load_prop<kReach>(A, v, dir);
+        // BFS entries of a local search carry the distance they were given
+        // (aux); a later decrease by another task re-queues the vertex there,
+        // so expanding with this value is exact and saves a dependent load
+        prop = (!kReach && !from_bag) ? (unsigned long long)(aux + 1u) : load_prop<kReach>(A, v, dir);
         if (ell != nullptr) {
             use_row = true;
             const uint4 *rp = reinterpret_cast<const uint4 *>(ell + (size_t)v * W);
@@ -433,21 +498,33 @@ __device__ void expand_wave(const TravArgs &A, const Round &R, const WarpSm &S, 
             nvalid += ok ? 1u : 0u;
             old[j] = relax_issue<kReach>(A, row[j], dir, prop, ok);
         }
+        // children inside the window are expanded next by this SM: start
+        // fetching their padded rows while the atomics are in flight
+        if (row_lane && ok_local) {
+#pragma unroll
+            for (int j = 0; j < (int)kMaxW; j++)
+                if ((uint32_t)j < W && row[j] < 0x80000000u) pg_prefetch_l1(ell + (size_t)row[j] * W);
+        }
 #pragma unroll
         for (int j = 0; j < (int)kMaxW; j++) imp[j] = improved<kReach>(prop, old[j]);
         if (row_lane) { C.expansions++; C.exp_verts++; C.exp_edges += nvalid; }
         const uint32_t wmax = max(A.ellw0, A.ellw1);
+        if (T.cta_n != nullptr) {
+            stage_rows<kReach>(A, R, S, T, imp, row, dir, caux, ok_local, wmax, lane, C);
+        } else {
 #pragma unroll
-        for (int j = 0; j < (int)kMaxW; j++) {
-            if ((uint32_t)j < wmax)
-                stage<kReach>(A, R, S, T, imp[j], kReach ? (row[j] | (dir << 31)) : row[j],
-                              caux, ok_local, lane, C);
+            for (int j = 0; j < (int)kMaxW; j++) {
+                if ((uint32_t)j < wmax)
+                    stage<kReach>(A, R, S, T, imp[j], kReach ? (row[j] | (dir << 31)) : row[j],
+                                  caux, ok_local, lane, C);
+            }
         }
     }
     if (__any_sync(kFull, hub_repush))
         stage<kReach>(A, R, S, T, hub_repush, entry, kReach ? aux : (uint32_t)(prop - 1), false,
                       lane, C);
     // CSR rows: the wave's edges laid end to end, dealt 32 per step
+    if (!__any_sync(kFull, deg != 0u)) return;
     const uint32_t incl = warp_incl_scan(deg, lane);
     const uint32_t total = __shfl_sync(kFull, incl, 31);
     if (total == 0) return;
@@ -550,10 +627,14 @@ __device__ void cta_round(const TravArgs &A, const Round &R, const WarpSm &S, co
         if (threadIdx.x == 0) {
             Q.n[0] = c;
             Q.n[1] = 0;
+            Q.n[2] = 0;
         }
         __syncthreads();
+        // level h reads buffer h%3 and appends to (h+1)%3; buffer (h+2)%3 was
+        // last touched in level h-1, so it is cleared here for level h+1,
+        // and one CTA barrier per level suffices
         for (uint32_t h = 0;; h++) {
-            const uint32_t cl = h & 1u, nl = cl ^ 1u;
+            const uint32_t cl = h % 3u, nl = (h + 1u) % 3u, ql = (h + 2u) % 3u;
             const uint32_t ncur = min(Q.n[cl], QC);
             if (ncur == 0) break;
             T.cta_ent = Q.ent[nl];
@@ -566,8 +647,7 @@ __device__ void cta_round(const TravArgs &A, const Round &R, const WarpSm &S, co
                 const uint32_t ax = (i < ncur) ? Q.aux[cl][i] : 0u;
                 expand_wave<kReach>(A, R, S, T, e, ax, h == 0, lane, C);
             }
-            __syncthreads();
-            if (threadIdx.x == 0) Q.n[cl] = 0;
+            if (threadIdx.x == 0) Q.n[ql] = 0;
             __syncthreads();
         }
         T.cta_n = nullptr;
@@ -806,12 +886,12 @@ __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
     CtaSm Q;
     {
         uint32_t *cta = s_u32 + (size_t)nwib * per_warp;
-        Q.ent[0] = cta;
-        Q.ent[1] = cta + A.L.cta_queue;
-        Q.aux[0] = cta + 2u * A.L.cta_queue;
-        Q.aux[1] = cta + 3u * A.L.cta_queue;
-        Q.n = cta + 4u * A.L.cta_queue;
-        Q.task = Q.n + 2;
+        for (int b = 0; b < 3; b++) {
+            Q.ent[b] = cta + (uint32_t)(2 * b) * A.L.cta_queue;
+            Q.aux[b] = cta + (uint32_t)(2 * b + 1) * A.L.cta_queue;
+        }
+        Q.n = cta + 6u * A.L.cta_queue;
+        Q.task = Q.n + 3;
     }
 
     if (A.L.schedule == PG_SCHED_LEARNED)
@@ -1065,7 +1145,7 @@ __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
 size_t traverse_smem(uint32_t threads, uint32_t qcap, uint32_t cta_queue) {
     const uint32_t nw = threads / 32;
     return 6144 + (size_t)nw * 256 + (size_t)nw * (4u * 32u + 2u * kSpillCap + 2u * qcap) * 4u +
-           (size_t)(4u * cta_queue + 4u) * 4u;
+           (size_t)(6u * cta_queue + 4u) * 4u;
 }
 
 template <bool kReach>

@@ -43,7 +43,8 @@ INF = 0xFFFFFFFF
 
 
 def training_graphs(quick: bool):
-    """Seeded training families: grids (aspect 1:1 .. 1:1000), kNN (k 2..10), R-MAT."""
+    """Seeded training families: grids (aspect 1:1 .. 1:1000), kNN (k 2..10), R-MAT
+    and path-like strips."""
     fams = [
         ("grid_1000x1000", lambda: gg.grid(1000, 1000)),
         ("grid_300x3000", lambda: gg.grid(300, 3000)),
@@ -64,8 +65,16 @@ def training_graphs(quick: bool):
             ("knn_3m_k4", lambda: gg.knn(3_000_000, 4, 108)),
             ("rmat_18", lambda: gg.rmat(18, 16, 109)),
             ("rmat_20", lambda: gg.rmat(20, 16, 110)),
+            # path-like strips: frontiers of one or two vertices for
+            # hundreds of thousands of rounds (the adversarial chain)
+            ("strip_300k", lambda: gg.strip(300_000)),
+            ("grid_2x150000", lambda: gg.grid(2, 150_000)),
         ]
     return fams
+
+
+# Strips are slow to roll out (one level per hop); fewer sources and states.
+FEW_STATES = {"strip_300k": (1, 5), "grid_2x150000": (1, 5)}
 
 
 def collect(G, src, base_tau=16, points=10, reps=2, hold=80_000):
@@ -83,7 +92,8 @@ def collect(G, src, base_tau=16, points=10, reps=2, hold=80_000):
     for r in rs:
         T, feat = {}, None
         for a in range(pg.PG_NUM_ACTIONS):
-            script = np.array([base_a] * r + [a] * hold, dtype=np.uint8)
+            # the script wraps around, so the held part outlasts any run
+            script = np.array([base_a] * r + [a] * max(hold, G.n + 64), dtype=np.uint8)
             buf = (pg.RoundTrace * (r + 1))()
             cfg = pg.default_config(schedule=pg.PG_SCHED_SCRIPT, script_len=len(script),
                                     trace_cap=r + 1)
@@ -188,8 +198,9 @@ def main():
     for name, make in training_graphs(args.quick):
         g = make()
         G = pg.Graph.from_graphgen(g, ell=True)
-        for src in gg.pick_sources(g, args.sources, 7):
-            X, A, Y = collect(G, int(src), points=args.points)
+        nsrc, npts = FEW_STATES.get(name, (args.sources, args.points))
+        for src in gg.pick_sources(g, nsrc, 7):
+            X, A, Y = collect(G, int(src), points=npts)
             Xs.append(X); As.append(A); Ys.append(Y)
             best = [int(np.argmax(Y[i:i + 8])) for i in range(0, len(Y), 8)]
             log(f"{name} src={int(src)} states={len(Y) // 8} best actions={best}")
@@ -203,7 +214,8 @@ def main():
         for name, make in (("knn_2m_k5_heldout", lambda: gg.knn(2_000_000, 5, 901)),
                            ("knn_2m_k3_heldout", lambda: gg.knn(2_000_000, 3, 902)),
                            ("grid_1000x1000", lambda: gg.grid(1000, 1000)),
-                           ("rmat_18_heldout", lambda: gg.rmat(18, 16, 903))):
+                           ("rmat_18_heldout", lambda: gg.rmat(18, 16, 903)),
+                           ("strip_1m", lambda: gg.strip(1_000_000))):
             g = make()
             G = pg.Graph.from_graphgen(g, ell=True)
             res = evaluate(G, 0, W)

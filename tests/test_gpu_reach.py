@@ -92,3 +92,31 @@ def test_bfs_multi_duplicate_sources(pg):
     srcs = np.array([3, 3, 9, 3], dtype=np.uint32)
     D = pg.to_uint32(G.bfs_multi(srcs))
     assert np.array_equal(D, oracle.bfs_multi(g, srcs))
+
+
+def _heavy_directed():
+    """Directed graph with hubs far above the chunk size in both directions."""
+    rng = np.random.default_rng(12)
+    n = 20_000
+    src = [rng.integers(0, n, 60_000)]
+    dst = [rng.integers(0, n, 60_000)]
+    src.append(np.full(5000, 7)); dst.append(rng.integers(0, n, 5000))        # out-hub
+    src.append(rng.integers(0, n, 3000)); dst.append(np.full(3000, 11))       # in-hub
+    src.append(np.arange(0, 900)); dst.append(np.arange(1, 901))              # a chain
+    return gg.from_arcs(n, np.concatenate(src), np.concatenate(dst), directed=True)
+
+
+def test_bfs_multi_heavy_directed(pg):
+    """Chunked high-degree vertices, top-down and bottom-up, on a directed graph."""
+    g = _heavy_directed()
+    G = pg.Graph.from_graphgen(g)
+    srcs = np.concatenate([[7, 11, 0], gg.pick_sources(g, 61, 6)]).astype(np.uint32)
+    want = oracle.bfs_multi(g, srcs)
+    for direction in (0, 1):
+        D = pg.to_uint32(G.bfs_multi(srcs, cfg=pg.default_config(direction=direction)))
+        assert np.array_equal(D, want), direction
+    # replacing the transpose rebuilds the in-edge chunk lists
+    toff, tidx = oracle.transpose(g)
+    G.set_transpose(toff, tidx)
+    D = pg.to_uint32(G.bfs_multi(srcs, cfg=pg.default_config(direction=1)))
+    assert np.array_equal(D, want)
