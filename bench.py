@@ -39,6 +39,7 @@ WORKLOADS = {
     "grid_1000": ("grid_1000", 0, "1000x1000 undirected 4-neighbour grid; BFS from vertex 0"),
     "knn_30m_k3": ("knn_30m_k3", 0, "held-out kNN graph, 30M points, k=3, seed 5; BFS from 0"),
     "strip_20m": ("strip_20m", 0, "1 x 20M strip (path); BFS from vertex 0"),
+    "strip_200k": ("strip_200k", 0, "1 x 200k strip (path, per-hop latency profile); BFS from vertex 0"),
 }
 
 

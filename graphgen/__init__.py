@@ -212,3 +212,8 @@ def knn_30m_k3(npts: int = 30_000_000) -> Graph:
 def strip_20m(length: int = 20_000_000) -> Graph:
     """1 x 20M strip (a path)."""
     return strip(length)
+
+
+def strip_200k(length: int = 200_000) -> Graph:
+    """1 x 200k strip (a path): a small chain for per-hop latency profiles."""
+    return strip(length)

@@ -203,6 +203,29 @@ pg_status pg_bfs_multi(pg_graph *g, const uint32_t *sources, uint32_t k, uint32_
                        const pg_config *cfg, pg_stats *stats, void *stream);
 
 /*
+ * Strongly connected components (Sec. 2.1: parallel SCC built on
+ * reachability searches, each run with vertical granularity control; Sec. 2
+ * defines an SCC as a maximal vertex set in which every vertex reaches every
+ * other).  Forward-backward over all open parts at once: trimming, one pivot
+ * per part, forward and backward searches confined to the part with a
+ * tau-hop local queue per warp, split into three parts.  Needs the
+ * transpose (undirected graphs have it).
+ *  label_out:  n uint32, device or host memory; label_out[v] = the smallest
+ *              vertex id of v's SCC (deterministic, independent of cfg).
+ *  cfg:        tau (hop window of the local search), threads_per_block,
+ *              local_queue, timeout_ms (per wait) and seed (pivot
+ *              priorities) are used; NULL = defaults.
+ *  stats:      rounds = search rounds summed over iterations, expansions =
+ *              vertices expanded, kernel_ms = the whole computation; NULL ok.
+ *  iterations: number of pivot iterations (NULL ok).
+ * Errors: PG_ERR_UNSUPPORTED without a transpose, PG_ERR_TIMEOUT /
+ * PG_ERR_OVERFLOW from the device (output undefined).  Buffers are kept on
+ * the graph (about 32 bytes per vertex) until pg_graph_free.
+ */
+pg_status pg_scc(pg_graph *g, uint32_t *label_out, const pg_config *cfg, pg_stats *stats,
+                 uint32_t *iterations, void *stream);
+
+/*
  * Traversed-edge count for TEPS: *n_reached = #{v : dist[v] != 0xFFFFFFFF},
  * *m_reached = sum of their out-degrees.  dist: device, n entries.
  */

@@ -18,6 +18,9 @@ Contents:
                        queue BFS against an independent definition.
   * ``reached_edges``  (n_r, m_r): reached vertices and the sum of their
                        out-degrees, the traversed-edge count used for TEPS.
+  * ``scc``            strongly connected components by Tarjan's algorithm
+                       (the paper's sequential SCC baseline, Sec. 4 Setup),
+                       labelled by the smallest vertex id of each component.
   * ``mlp``            fp64 forward / backward / Adam of the schedule MLP.
 
 Parity status: every function here is pinned by closed forms, brute force
@@ -64,6 +67,7 @@ def _load():
         lib.oracle_floyd_warshall.argtypes = [u32, vp, vp, vp]
         lib.oracle_warshall.argtypes = [u32, vp, vp, vp]
         lib.oracle_reached_edges.argtypes = [u32, vp, vp, vp, vp]
+        lib.oracle_scc.argtypes = [u32, vp, vp, vp]
         lib.oracle_reached_edges.restype = None
         _lib = lib
     return _lib
@@ -136,3 +140,13 @@ def reached_edges(g, dist) -> tuple[int, int]:
     _load().oracle_reached_edges(g.n, off.ctypes.data, d.ctypes.data, ctypes.byref(a),
                                  ctypes.byref(b))
     return int(a.value), int(b.value)
+
+
+def scc(g) -> np.ndarray:
+    """Per-vertex SCC label: the smallest vertex id in the vertex's component."""
+    off, idx = _u32(g.offsets), _u32(g.indices)
+    lab = np.empty(g.n, dtype=np.uint32)
+    rc = _load().oracle_scc(g.n, off.ctypes.data, idx.ctypes.data, lab.ctypes.data)
+    if rc:
+        raise RuntimeError(f"oracle_scc failed ({rc})")
+    return lab

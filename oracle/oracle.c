@@ -18,6 +18,10 @@
  *    distances and transitive closure for tiny graphs; they pin the queue
  *    BFS itself (an independent definition of the same quantities).
  *  - oracle_transpose: reversed CSR, written here independently.
+ *  - oracle_scc: strongly connected components (Sec. 2: a maximal vertex
+ *    set in which every vertex reaches every other) by Tarjan's algorithm,
+ *    the paper's sequential SCC baseline (Sec. 4, Setup); each vertex is
+ *    labelled with the smallest vertex id of its component.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -160,4 +164,59 @@ void oracle_reached_edges(uint32_t n, const uint32_t *offsets, const uint32_t *d
     for (uint32_t v = 0; v < n; v++)
         if (dist[v] != OR_INF) { a++; b += offsets[v + 1] - offsets[v]; }
     *n_r = a; *m_r = b;
+}
+
+/* Strongly connected components by Tarjan's algorithm (Tarjan 1972), the
+ * paper's sequential SCC baseline (Sec. 4, Setup).  Iterative: an explicit
+ * DFS stack of (vertex, next arc) frames replaces the recursion.  label[v]
+ * is the smallest vertex id in v's component.  Returns 0, or -1/-2 on bad
+ * input / no memory. */
+int oracle_scc(uint32_t n, const uint32_t *offsets, const uint32_t *indices, uint32_t *label) {
+    if (n == 0 || !offsets || !label) return -1;
+    uint32_t *index = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+    uint32_t *low = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+    uint8_t *on = (uint8_t *)calloc(n, 1);
+    uint32_t *comp = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));   /* Tarjan's stack */
+    uint32_t *fv = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));     /* DFS frames: vertex */
+    uint32_t *fe = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));     /*             next arc */
+    if (!index || !low || !on || !comp || !fv || !fe) {
+        free(index); free(low); free(on); free(comp); free(fv); free(fe);
+        return -2;
+    }
+    for (uint32_t v = 0; v < n; v++) index[v] = OR_INF;
+    uint32_t counter = 0, sp = 0, depth = 0;
+    for (uint32_t s = 0; s < n; s++) {
+        if (index[s] != OR_INF) continue;
+        index[s] = low[s] = counter++;
+        comp[sp++] = s; on[s] = 1;
+        fv[0] = s; fe[0] = offsets[s]; depth = 1;
+        while (depth) {
+            const uint32_t v = fv[depth - 1];
+            if (fe[depth - 1] < offsets[v + 1]) {
+                const uint32_t w = indices[fe[depth - 1]++];
+                if (index[w] == OR_INF) {            /* tree arc: descend */
+                    index[w] = low[w] = counter++;
+                    comp[sp++] = w; on[w] = 1;
+                    fv[depth] = w; fe[depth] = offsets[w]; depth++;
+                } else if (on[w] && index[w] < low[v]) {
+                    low[v] = index[w];               /* arc back into the open stack */
+                }
+                continue;
+            }
+            /* all arcs of v done: v roots a component iff low == index */
+            depth--;
+            if (low[v] == index[v]) {
+                uint32_t top = sp, mn = OR_INF;
+                do { top--; if (comp[top] < mn) mn = comp[top]; } while (comp[top] != v);
+                for (uint32_t i = top; i < sp; i++) { on[comp[i]] = 0; label[comp[i]] = mn; }
+                sp = top;
+            }
+            if (depth) {
+                const uint32_t p = fv[depth - 1];
+                if (low[v] < low[p]) low[p] = low[v];
+            }
+        }
+    }
+    free(index); free(low); free(on); free(comp); free(fv); free(fe);
+    return 0;
 }

@@ -37,7 +37,7 @@ INF = 0xFFFFFFFF
 EXPORTS = ["pg_config_default", "pg_graph_upload", "pg_graph_set_transpose", "pg_graph_free",
            "pg_graph_info", "pg_bfs", "pg_reach_multi", "pg_bfs_multi", "pg_count_reached",
            "pg_set_schedule_weights", "pg_mlp_forward", "pg_mlp_backward", "pg_mlp_adam",
-           "pg_autotune", "pg_bfs_noalloc", "pg_last_error", "pg_version"]
+           "pg_autotune", "pg_bfs_noalloc", "pg_scc", "pg_last_error", "pg_version"]
 NOALLOC_MAX_N = 1 << 20
 
 
@@ -111,6 +111,7 @@ def load(path: str | None = None):
                                        ctypes.c_float, ctypes.c_float, vp]),
         "pg_autotune": (ctypes.c_int, [vp, u32, vp, u32, u32, u32, P(Config), vp]),
         "pg_bfs_noalloc": (ctypes.c_int, [vp, vp, u32, u32, u32, vp, P(Config), vp]),
+        "pg_scc": (ctypes.c_int, [vp, vp, P(Config), P(Stats), P(u32), vp]),
         "pg_last_error": (ctypes.c_char_p, []),
         "pg_version": (ctypes.c_char_p, []),
     }
@@ -245,6 +246,22 @@ class Graph:
                                    ctypes.byref(cfg) if cfg else None,
                                    ctypes.byref(stats) if stats else None, _stream_ptr(stream)))
         return out
+
+    def scc(self, out=None, cfg: Config | None = None, stats: Stats | None = None, stream=None):
+        """SCC labels (smallest vertex id of each component) as a CUDA int32
+        tensor (uint32 bits), and the number of pivot iterations."""
+        import torch
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        if isinstance(out, np.ndarray):  # host output: the library stages and copies back
+            assert out.dtype == np.uint32 and out.flags.c_contiguous and len(out) == self.n
+            ptr = ctypes.c_void_p(out.ctypes.data)
+        else:
+            ptr = ctypes.c_void_p(out.data_ptr())
+        it = ctypes.c_uint32()
+        _check(load().pg_scc(self._h, ptr, ctypes.byref(cfg) if cfg else None,
+                             ctypes.byref(stats) if stats else None, ctypes.byref(it), _stream_ptr(stream)))
+        return out, it.value
 
     def count_reached(self, dist, stream=None):
         a, b = ctypes.c_uint64(), ctypes.c_uint64()

@@ -396,6 +396,7 @@ static void release(pg_graph *g) {
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
     pg_msbfs_release(g);
+    pg_scc_release(g);
     delete g;
 }
 

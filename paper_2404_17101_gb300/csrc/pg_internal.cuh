@@ -154,6 +154,8 @@ int pg_device_sms(int dev);
     } while (0)
 
 struct PgMsbfsWork;  // batched BFS buffers (pg_msbfs.cu)
+struct PgSccWork;    // SCC buffers (pg_scc.cu)
+void pg_scc_release(pg_graph *g);
 void pg_msbfs_release(pg_graph *g);  // frees them; rebuilt on the next batched call
 
 struct pg_graph {
@@ -183,6 +185,7 @@ struct pg_graph {
     float *d_weights;
     bool has_weights;
     PgMsbfsWork *msbfs;
+    PgSccWork *scc;
     int num_sms;
     cudaEvent_t ev0, ev1;  // bracket the traversal kernel of the last call
 };

@@ -14,7 +14,8 @@ hold at any size:
     sampled bits against the oracle, and for every bit closure (mask[w]
     contains mask[u] on every arc u -> w) and minimality (mask[w] is the OR
     of its in-neighbours' masks plus its own source bits);
-  * C5 held-out kNN 30M (k = 3): the oracle; 1 x 20M strip: dist = index.
+  * C5 held-out kNN 30M (k = 3): the oracle; 1 x 20M strip: dist = index;
+  * SCC of the C4 grid against the oracle's Tarjan labels, every vertex.
 """
 import numpy as np
 import pytest
@@ -126,3 +127,12 @@ def test_c5_strip_20m(pg):
     G = pg.Graph.from_graphgen(g)
     d = pg.to_uint32(G.bfs(0, cfg=pg.default_config(tau=64, timeout_ms=20000)))
     assert np.array_equal(d, np.arange(g.n, dtype=np.uint32))
+
+
+def test_c4_dgrid_4000_scc(pg):
+    """SCC of the full directed grid with shortcuts, element by element."""
+    g = gg.dgrid_4000()
+    G = pg.Graph.from_graphgen(g, ell=True)
+    lab, it = G.scc()
+    assert np.array_equal(pg.to_uint32(lab), oracle.scc(g))
+    assert it >= 1
