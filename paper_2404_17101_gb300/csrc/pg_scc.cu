@@ -4,29 +4,33 @@
 // Sec. 2.1 builds parallel SCC on reachability searches, which need no BFS
 // order, and runs each search with VGC: a task keeps expanding locally for a
 // bounded number of hops before it hands vertices to the next round.  Here
-// the searches follow the forward-backward scheme, for every open subproblem
-// at once:
+// the searches decompose every open part of the graph at once (colouring):
 //   * every unfinished vertex carries a part label (a vertex id);
 //   * trimming: a vertex with no in-arc or no out-arc from another
 //     unfinished vertex of its part is an SCC on its own;
-//   * every part picks a pivot (largest hashed priority), and one
-//     cooperative launch runs the forward and the backward search of every
-//     pivot, each confined to the pivot's part, with a tau-hop local queue
-//     per warp;
-//   * vertices reached both ways form the pivot's SCC; the others split into
-//     three new parts (forward only, backward only, neither).  Two vertices
-//     of one SCC are always reached alike, so no part boundary ever cuts an
-//     SCC, and every iteration finishes at least every pivot.
-// The label of a vertex is the smallest vertex id of its SCC.
+//   * colouring: every vertex of a part gets a random key (priority << 32 |
+//     id), and a forward search propagates the largest key along the arcs
+//     inside the part (atomicMax, label-correcting to a fixpoint); a vertex
+//     ends with the largest key among the vertices that reach it;
+//   * a vertex whose final key is its own is a root; a backward search from
+//     every root, confined to the vertices of its colour, finds exactly the
+//     root's SCC (they reach the root, and the root reaches them because its
+//     key flowed to them);
+//   * the rest take their colour's root as their new part: the vertices of
+//     one SCC have the same ancestors, hence the same colour, so no part
+//     boundary ever cuts an SCC.  Every part holds at least one root (its
+//     largest key), so every iteration finishes vertices.
+// Both searches run in one persistent cooperative kernel each, with a
+// tau-hop local queue per warp and round tags that keep each vertex at most
+// once per bag.  The label of a vertex is the smallest vertex id of its SCC.
 #include "pg_internal.cuh"
 
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr uint32_t kDir = 0x80000000u;  // bag entry bit: backward search
 constexpr int kMaxWarps = 16;
 
-// murmur3's 32-bit finaliser (Appleby, public domain): pivot priorities
+// murmur3's 32-bit finaliser (Appleby, public domain): vertex priorities
 __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
     h ^= h >> 16;
     h *= 0x85ebca6bu;
@@ -34,6 +38,10 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
     h *= 0xc2b2ae35u;
     h ^= h >> 16;
     return h;
+}
+
+__device__ __forceinline__ unsigned long long scc_key(uint32_t v, uint32_t seed) {
+    return ((unsigned long long)fmix32(v ^ seed) << 32) | v;
 }
 
 __global__ void k_scc_init(uint32_t n, uint32_t *part, uint32_t *rep) {
@@ -71,23 +79,28 @@ __global__ void k_scc_trim(const uint32_t *off, const uint32_t *idx, const uint3
     }
 }
 
-// piv[P] = max over unfinished v of part P of (priority(v) << 32 | v)
-__global__ void k_scc_pivot(uint32_t n, const uint32_t *part, unsigned long long *piv, uint32_t seed) {
+__global__ void k_scc_color_init(uint32_t n, const uint32_t *part, unsigned long long *col, uint32_t seed) {
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-        const uint32_t P = part[v];
-        if (P == PG_NONE) continue;
-        const unsigned long long key = ((unsigned long long)fmix32(v ^ seed) << 32) | v;
-        atomicMax(piv + P, key);
-    }
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        if (part[v] != PG_NONE) col[v] = scc_key(v, seed);
+}
+
+// roots: the vertices whose final colour is their own key
+__global__ void k_scc_roots(uint32_t n, const uint32_t *part, const unsigned long long *col,
+                            uint32_t *flag, uint32_t seed) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        if (part[v] != PG_NONE) flag[v] = (col[v] == scc_key(v, seed)) ? 1u : 0u;
 }
 
 struct SccArgs {
     const uint32_t *off, *idx, *toff, *tidx;
     uint32_t n;
     const uint32_t *part;
-    uint32_t *flag;                   // bit 0: reached forward, bit 1: reached backward
-    const unsigned long long *piv;
+    unsigned long long *col;          // colour (largest key reaching the vertex)
+    uint32_t *flag;                   // 1: in its root's SCC (backward search)
+    uint32_t *stamp;                  // round tags: one bag entry per vertex and round
+    uint32_t tag0;
     uint32_t *bag;                    // [2][cap]
     uint32_t cap;
     PgCtrl *ctrl;
@@ -96,13 +109,16 @@ struct SccArgs {
 };
 
 struct SccWarp {
-    uint32_t *s_incl, *s_base, *s_part, *s_ent, *s_hop;  // [32] each
-    uint32_t *lq, *lh;                                    // local queue [qcap] entries, hops
+    uint32_t *s_incl, *s_base, *s_part, *s_hop;  // [32] each
+    unsigned long long *s_col;                   // [32]
+    uint32_t *lq, *lh;                           // local queue [qcap]: vertex, hops
 };
 
-// Append the lanes' `go` entries to the next bag (one atomic per warp).
-__device__ __forceinline__ void scc_push(const SccArgs &A, PgSlot *sn, uint32_t nxt, bool go,
-                                         uint32_t ent, int lane) {
+// Append the lanes' `go` vertices to the next bag (one atomic per warp);
+// `dedupe`: a vertex already appended in this round is skipped.
+__device__ __forceinline__ void scc_push(const SccArgs &A, PgSlot *sn, uint32_t nxt, uint32_t tag,
+                                         bool go, bool dedupe, uint32_t v, int lane) {
+    if (go && dedupe) go = atomicExch(A.stamp + v, tag) != tag;
     const unsigned bal = __ballot_sync(kFull, go);
     if (!bal) return;
     uint32_t pos = 0;
@@ -110,27 +126,32 @@ __device__ __forceinline__ void scc_push(const SccArgs &A, PgSlot *sn, uint32_t 
     pos = __shfl_sync(kFull, pos, 0);
     if (go) {
         const uint32_t p = pos + __popc(bal & pg_lanemask_lt());
-        if (p < A.cap) A.bag[(size_t)nxt * A.cap + p] = ent;
+        if (p < A.cap) A.bag[(size_t)nxt * A.cap + p] = v;
         else atomicOr(&A.ctrl->status, PG_DEV_OVERFLOW);
     }
 }
 
-// Expand one wave (one entry per lane, hop count h): every arc to an
-// unfinished vertex of the same part sets the direction's bit; a vertex
-// whose bit was new is searched on, locally while its hop count stays below
-// tau and the local queue has room, else in the next round.
-__device__ void scc_wave(const SccArgs &A, const SccWarp &S, PgSlot *sn, uint32_t nxt,
-                         uint32_t ent, uint32_t hop, int lane, uint32_t &qhead, uint32_t &qtail,
+// Expand one wave (one vertex per lane, hop count h).
+//  kColor: forward arcs inside the part carry the vertex's current colour
+//          (atomicMax); a raised colour is searched on.
+//  else:   backward arcs to unfinished vertices of the same colour set the
+//          SCC flag; a newly flagged vertex is searched on.
+// Searched-on vertices stay in the warp's local queue while their hop count
+// is below tau and it has room, else they go to the next round's bag.
+template <bool kColor>
+__device__ void scc_wave(const SccArgs &A, const SccWarp &S, PgSlot *sn, uint32_t nxt, uint32_t tag,
+                         uint32_t v, uint32_t hop, int lane, uint32_t &qhead, uint32_t &qtail,
                          unsigned long long &exp) {
-    const bool valid = ent != PG_NONE;
-    const uint32_t v = ent & ~kDir;
-    const uint32_t dir = ent >> 31;
+    const bool valid = v != PG_NONE;
+    const uint32_t *off = kColor ? A.off : A.toff;
+    const uint32_t *idx = kColor ? A.idx : A.tidx;
     uint32_t beg = 0, deg = 0, P = PG_NONE;
+    unsigned long long c = 0;
     if (valid) {
-        const uint32_t *o = dir ? A.toff : A.off;
-        beg = __ldg(o + v);
-        deg = __ldg(o + v + 1) - beg;
+        beg = __ldg(off + v);
+        deg = __ldg(off + v + 1) - beg;
         P = __ldg(A.part + v);
+        c = __ldcg(A.col + v);
         exp++;
     }
     uint32_t incl = deg;
@@ -145,27 +166,29 @@ __device__ void scc_wave(const SccArgs &A, const SccWarp &S, PgSlot *sn, uint32_
     S.s_incl[lane] = incl;
     S.s_base[lane] = beg - (incl - deg);  // u32: wraps, and the sum below unwraps
     S.s_part[lane] = P;
-    S.s_ent[lane] = dir ? kDir : 0u;
     S.s_hop[lane] = hop;
+    S.s_col[lane] = c;
     __syncwarp();
     for (uint32_t base = 0; base < total; base += 32u) {
         const uint32_t j = base + (uint32_t)lane;
         bool imp = false, local = false;
-        uint32_t went = 0, wh = 0;
+        uint32_t w = 0, wh = 0;
         if (j < total) {
             uint32_t o = 0;
 #pragma unroll
             for (uint32_t step = 16; step >= 1; step >>= 1)
                 if (S.s_incl[o + step - 1] <= j) o += step;
-            const uint32_t d = S.s_ent[o];
             const uint32_t e = S.s_base[o] + j;
-            const uint32_t w = __ldg((d ? A.tidx : A.idx) + e);
+            w = __ldg(idx + e);
             const uint32_t pw = __ldg(A.part + w);
+            const unsigned long long co = S.s_col[o];
             if (pw == S.s_part[o] && pw != PG_NONE) {
-                const uint32_t bit = d ? 2u : 1u;
-                imp = (atomicOr(A.flag + w, bit) & bit) == 0u;
+                if (kColor) {
+                    imp = atomicMax(A.col + w, co) < co;
+                } else if (__ldcg(A.col + w) == co) {
+                    imp = (atomicOr(A.flag + w, 1u) & 1u) == 0u;
+                }
             }
-            went = w | d;
             wh = S.s_hop[o] + 1u;
             local = imp && wh < A.tau;
         }
@@ -176,28 +199,31 @@ __device__ void scc_wave(const SccArgs &A, const SccWarp &S, PgSlot *sn, uint32_
         const bool to_q = local && rank < room;
         if (to_q) {
             const uint32_t p = (qtail + rank) & (A.qcap - 1u);
-            S.lq[p] = went;
+            S.lq[p] = w;
             S.lh[p] = wh;
         }
         qtail += min((uint32_t)__popc(bl), room);
-        scc_push(A, sn, nxt, imp && !to_q, went, lane);
+        scc_push(A, sn, nxt, tag, imp && !to_q, kColor, w, lane);
     }
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(512, 1) k_scc_reach(const SccArgs A) {
+// One search to its fixpoint.  Seeds: kColor, every unfinished vertex;
+// else every root (flag == 1).
+template <bool kColor>
+__global__ void __launch_bounds__(512, 1) k_scc_search(const SccArgs A) {
     extern __shared__ __align__(16) uint32_t sm[];
     __shared__ int s_flag;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const uint32_t per_warp = 5u * 32u + 2u * A.qcap;
+    const uint32_t per_warp = 6u * 32u + 2u * A.qcap;
     uint32_t *mine = sm + (size_t)wib * per_warp;
     SccWarp S;
-    S.s_incl = mine;
-    S.s_base = mine + 32;
-    S.s_part = mine + 64;
-    S.s_ent = mine + 96;
-    S.s_hop = mine + 128;
-    S.lq = mine + 160;
+    S.s_col = reinterpret_cast<unsigned long long *>(mine);  // 64 words, 8-byte aligned
+    S.s_incl = mine + 64;
+    S.s_base = mine + 96;
+    S.s_part = mine + 128;
+    S.s_hop = mine + 160;
+    S.lq = mine + 192;
     S.lh = S.lq + A.qcap;
     PgCtrl *ctrl = A.ctrl;
     unsigned gen = 0;
@@ -205,19 +231,11 @@ __global__ void __launch_bounds__(512, 1) k_scc_reach(const SccArgs A) {
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t gthreads = gridDim.x * blockDim.x;
 
-    // seeds: every part's pivot, forward and backward
     for (uint32_t b0 = gtid - (uint32_t)lane; b0 < n; b0 += gthreads) {
         const uint32_t v = b0 + (uint32_t)lane;
-        bool piv = false;
-        if (v < n) {
-            const uint32_t P = __ldg(A.part + v);
-            if (P != PG_NONE) {
-                piv = (uint32_t)A.piv[P] == v;
-                A.flag[v] = piv ? 3u : 0u;
-            }
-        }
-        scc_push(A, &ctrl->slot[0], 0u, piv, v, lane);
-        scc_push(A, &ctrl->slot[0], 0u, piv, v | kDir, lane);
+        bool seed = false;
+        if (v < n && __ldg(A.part + v) != PG_NONE) seed = kColor ? true : (A.flag[v] == 1u);
+        scc_push(A, &ctrl->slot[0], 0u, 0u, seed, false, v, lane);
     }
     if (!pg_grid_sync(ctrl, gridDim.x, gen, A.timeout_ns, &s_flag)) return;
 
@@ -228,9 +246,10 @@ __global__ void __launch_bounds__(512, 1) k_scc_reach(const SccArgs A) {
         PgSlot *sc = &ctrl->slot[r % PG_NUM_SLOTS];
         PgSlot *sn = &ctrl->slot[(r + 1) % PG_NUM_SLOTS];
         const uint32_t cur = r & 1u, nxt = cur ^ 1u;
+        const uint32_t tag = A.tag0 + r + 1u;
         const uint32_t F = __ldcg(&sc->size);
         if (F == 0) break;
-        if (F > A.cap) {
+        if (F > A.cap || tag == 0u) {
             if (gtid == 0) atomicOr(&ctrl->status, PG_DEV_OVERFLOW);
             break;
         }
@@ -245,17 +264,17 @@ __global__ void __launch_bounds__(512, 1) k_scc_reach(const SccArgs A) {
             if (lane == 0) base = atomicAdd(&sc->head, 32u);
             base = __shfl_sync(kFull, base, 0);
             if (base >= F) break;
-            uint32_t ent = (base + lane < F) ? __ldcg(A.bag + (size_t)cur * A.cap + base + lane) : PG_NONE;
+            uint32_t v = (base + lane < F) ? __ldcg(A.bag + (size_t)cur * A.cap + base + lane) : PG_NONE;
             uint32_t hop = 0;
             uint32_t qhead = 0, qtail = 0;
             for (;;) {
-                scc_wave(A, S, sn, nxt, ent, hop, lane, qhead, qtail, exp);
+                scc_wave<kColor>(A, S, sn, nxt, tag, v, hop, lane, qhead, qtail, exp);
                 const uint32_t avail = qtail - qhead;
                 if (avail == 0) break;
                 const uint32_t take = min(32u, avail);
                 __syncwarp();
                 const uint32_t p = (qhead + lane) & (A.qcap - 1u);
-                ent = ((uint32_t)lane < take) ? S.lq[p] : PG_NONE;
+                v = ((uint32_t)lane < take) ? S.lq[p] : PG_NONE;
                 hop = ((uint32_t)lane < take) ? S.lh[p] : 0u;
                 qhead += take;
                 __syncwarp();
@@ -268,35 +287,22 @@ __global__ void __launch_bounds__(512, 1) k_scc_reach(const SccArgs A) {
     if (gtid == 0) ctrl->rounds = r;
 }
 
-// Finished both ways -> the pivot's SCC; else the vertex joins the new part
-// (old part, class), named by its smallest vertex (tbl[3 P + class]).
-__global__ void k_scc_split_a(uint32_t n, uint32_t *part, uint32_t *flag,
-                              const unsigned long long *piv, uint32_t *rep, uint32_t *tbl) {
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-        const uint32_t P = part[v];
-        if (P == PG_NONE) continue;
-        const uint32_t f = flag[v] & 3u;
-        if (f == 3u) {
-            rep[v] = (uint32_t)piv[P];
-            part[v] = PG_NONE;
-        } else {
-            const uint32_t cls = (f & 1u) ? 1u : ((f & 2u) ? 2u : 0u);
-            atomicMin(tbl + 3ull * P + cls, v);
-            flag[v] = cls;
-        }
-    }
-}
-
-__global__ void k_scc_split_b(uint32_t n, uint32_t *part, const uint32_t *flag, const uint32_t *tbl,
-                              unsigned *active) {
+// Flagged -> finished in its root's SCC; else the colour's root names the
+// vertex's new part.  Counts the unfinished vertices.
+__global__ void k_scc_assign(uint32_t n, uint32_t *part, const unsigned long long *col,
+                             const uint32_t *flag, uint32_t *rep, unsigned *active) {
     const uint32_t stride = gridDim.x * blockDim.x;
     unsigned cnt = 0;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-        const uint32_t P = part[v];
-        if (P == PG_NONE) continue;
-        part[v] = tbl[3ull * P + flag[v]];
-        cnt++;
+        if (part[v] == PG_NONE) continue;
+        const uint32_t root = (uint32_t)col[v];
+        if (flag[v] == 1u) {
+            rep[v] = root;
+            part[v] = PG_NONE;
+        } else {
+            part[v] = root;
+            cnt++;
+        }
     }
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
     if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(active, cnt);
@@ -315,22 +321,49 @@ __global__ void k_scc_label(uint32_t n, const uint32_t *rep, const uint32_t *mn,
 }  // namespace
 
 struct PgSccWork {
-    uint32_t *part, *rep, *flag, *tbl;
-    unsigned long long *piv;
+    uint32_t *part, *rep, *flag, *mn;
+    unsigned long long *col;
     unsigned *counter;
 };
 
 void pg_scc_release(pg_graph *g) {
     if (g && g->scc) {
         cudaFree(g->scc->part);
-        cudaFree(g->scc->piv);
+        cudaFree(g->scc->col);
         delete g->scc;
         g->scc = nullptr;
     }
 }
 
 static size_t scc_smem(uint32_t threads, uint32_t qcap) {
-    return (size_t)(threads / 32u) * (5u * 32u + 2u * qcap) * sizeof(uint32_t);
+    return (size_t)(threads / 32u) * (6u * 32u + 2u * qcap) * sizeof(uint32_t);
+}
+
+template <bool kColor>
+static pg_status scc_search(pg_graph *g, SccArgs &A, uint32_t threads, size_t smem, cudaStream_t s,
+                            uint32_t *rounds, unsigned long long *expansions) {
+    // round tags of this launch: epoch + r + 1; restart the tags before they wrap
+    if (g->epoch > 0xE0000000u) {
+        PG_CK(cudaMemsetAsync(g->d_stamp, 0, (size_t)2 * g->n * sizeof(uint32_t), s));
+        g->epoch = 1;
+    }
+    A.tag0 = g->epoch;
+    PG_CK(cudaMemsetAsync(g->d_ctrl, 0, sizeof(PgCtrl), s));
+    void *args[] = {(void *)&A};
+    PG_CK(cudaLaunchCooperativeKernel((const void *)k_scc_search<kColor>, dim3((uint32_t)g->num_sms),
+                                      dim3(threads), args, smem, s));
+    const size_t off = offsetof(PgCtrl, status);
+    PG_CK(cudaMemcpyAsync((char *)g->h_ctrl + off, (const char *)g->d_ctrl + off, sizeof(PgCtrl) - off,
+                          cudaMemcpyDeviceToHost, s));
+    PG_CK(cudaStreamSynchronize(s));
+    const PgCtrl &h = *g->h_ctrl;
+    g->epoch += h.rounds + 2u;
+    *rounds += h.rounds;
+    *expansions += h.expansions;
+    if (h.status & PG_DEV_TIMEOUT)
+        return pg_set_error(PG_ERR_TIMEOUT, "device wait exceeded %llu ms (SCC search)", A.timeout_ns / 1000000ull);
+    if (h.status & PG_DEV_OVERFLOW) return pg_set_error(PG_ERR_OVERFLOW, "frontier capacity exceeded (SCC search)");
+    return PG_OK;
 }
 
 extern "C" pg_status pg_scc(pg_graph *g, uint32_t *label_out, const pg_config *cfg, pg_stats *stats,
@@ -358,8 +391,8 @@ extern "C" pg_status pg_scc(pg_graph *g, uint32_t *label_out, const pg_config *c
         PgSccWork *W = new PgSccWork();
         memset(W, 0, sizeof(*W));
         uint32_t *p = nullptr;
-        cudaError_t e = cudaMalloc(&p, ((size_t)6 * n + 8) * sizeof(uint32_t));
-        if (e == cudaSuccess) e = cudaMalloc(&W->piv, (size_t)n * sizeof(unsigned long long));
+        cudaError_t e = cudaMalloc(&p, ((size_t)4 * n + 8) * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&W->col, (size_t)n * sizeof(unsigned long long));
         if (e != cudaSuccess) {
             cudaFree(p);
             delete W;
@@ -368,8 +401,8 @@ extern "C" pg_status pg_scc(pg_graph *g, uint32_t *label_out, const pg_config *c
         W->part = p;
         W->rep = p + n;
         W->flag = p + 2 * (size_t)n;
-        W->tbl = p + 3 * (size_t)n;               // 3n group minima
-        W->counter = p + 6 * (size_t)n;
+        W->mn = p + 3 * (size_t)n;
+        W->counter = p + 4 * (size_t)n;
         g->scc = W;
     }
     PgSccWork &W = *g->scc;
@@ -382,11 +415,14 @@ extern "C" pg_status pg_scc(pg_graph *g, uint32_t *label_out, const pg_config *c
         out = (uint32_t *)p;
     }
     const size_t smem = scc_smem(threads, qcap);
-    PG_CK(cudaFuncSetAttribute(k_scc_reach, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    PG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scc_reach, threads, smem));
-    if (per_sm < 1) return pg_set_error(PG_ERR_INVALID_ARG, "SCC search does not fit an SM (threads %u, queue %u)", threads, qcap);
-    const uint32_t blocks = (uint32_t)g->num_sms;  // one CTA per SM
+    for (int k = 0; k < 2; k++) {
+        const void *kern = k ? (const void *)k_scc_search<true> : (const void *)k_scc_search<false>;
+        PG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        PG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+        if (per_sm < 1)
+            return pg_set_error(PG_ERR_INVALID_ARG, "SCC search does not fit an SM (threads %u, queue %u)", threads, qcap);
+    }
     const int grid = g->num_sms * 4;
 
     SccArgs A;
@@ -397,8 +433,9 @@ extern "C" pg_status pg_scc(pg_graph *g, uint32_t *label_out, const pg_config *c
     A.tidx = g->d_tidx;
     A.n = n;
     A.part = W.part;
+    A.col = W.col;
     A.flag = W.flag;
-    A.piv = W.piv;
+    A.stamp = g->d_stamp;
     A.bag = g->d_bag;
     A.cap = g->bag_cap;
     A.ctrl = g->d_ctrl;
@@ -411,42 +448,29 @@ extern "C" pg_status pg_scc(pg_graph *g, uint32_t *label_out, const pg_config *c
     PG_CK(cudaGetLastError());
     uint32_t iter = 0, rounds = 0;
     unsigned long long expansions = 0;
-    const uint32_t max_iter = n + 1;
     for (;; iter++) {
-        if (iter >= max_iter) return pg_set_error(PG_ERR_OVERFLOW, "SCC did not finish in %u iterations", max_iter);
-        for (int t = 0; t < 2; t++)
-            k_scc_trim<<<grid, 256, 0, s>>>(g->d_off, g->d_idx, g->d_toff, g->d_tidx, n, W.part, W.rep);
-        PG_CK(cudaMemsetAsync(W.piv, 0, (size_t)n * sizeof(unsigned long long), s));
-        k_scc_pivot<<<grid, 256, 0, s>>>(n, W.part, W.piv, c->seed * 0x9E3779B9u + iter);
+        if (iter > n) return pg_set_error(PG_ERR_OVERFLOW, "SCC did not finish in %u iterations", n + 1);
+        const uint32_t seed = (c->seed + 1u) * 0x9E3779B9u + iter * 0x85EBCA6Bu;
+        k_scc_trim<<<grid, 256, 0, s>>>(g->d_off, g->d_idx, g->d_toff, g->d_tidx, n, W.part, W.rep);
+        k_scc_color_init<<<grid, 256, 0, s>>>(n, W.part, W.col, seed);
         PG_CK(cudaGetLastError());
-        PG_CK(cudaMemsetAsync(g->d_ctrl, 0, sizeof(PgCtrl), s));
-        void *args[] = {(void *)&A};
-        PG_CK(cudaLaunchCooperativeKernel((const void *)k_scc_reach, dim3(blocks), dim3(threads), args, smem, s));
-        PG_CK(cudaMemsetAsync(W.tbl, 0xFF, (size_t)3 * n * sizeof(uint32_t), s));
+        pg_status st = scc_search<true>(g, A, threads, smem, s, &rounds, &expansions);
+        if (st) return st;
+        k_scc_roots<<<grid, 256, 0, s>>>(n, W.part, W.col, W.flag, seed);
+        PG_CK(cudaGetLastError());
+        st = scc_search<false>(g, A, threads, smem, s, &rounds, &expansions);
+        if (st) return st;
         PG_CK(cudaMemsetAsync(W.counter, 0, sizeof(unsigned), s));
-        k_scc_split_a<<<grid, 256, 0, s>>>(n, W.part, W.flag, W.piv, W.rep, W.tbl);
-        k_scc_split_b<<<grid, 256, 0, s>>>(n, W.part, W.flag, W.tbl, W.counter);
+        k_scc_assign<<<grid, 256, 0, s>>>(n, W.part, W.col, W.flag, W.rep, W.counter);
         PG_CK(cudaGetLastError());
-        // status of the search and the number of unfinished vertices
-        const size_t off = offsetof(PgCtrl, status);
-        PG_CK(cudaMemcpyAsync((char *)g->h_ctrl + off, (const char *)g->d_ctrl + off, sizeof(PgCtrl) - off,
-                              cudaMemcpyDeviceToHost, s));
         unsigned active = 0;
         PG_CK(cudaMemcpyAsync(&active, W.counter, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         PG_CK(cudaStreamSynchronize(s));
-        const PgCtrl &h = *g->h_ctrl;
-        rounds += h.rounds;
-        expansions += h.expansions;
-        if (h.status & PG_DEV_TIMEOUT)
-            return pg_set_error(PG_ERR_TIMEOUT, "device wait exceeded %llu ms (SCC iteration %u)",
-                                timeout_ns / 1000000ull, iter);
-        if (h.status & PG_DEV_OVERFLOW)
-            return pg_set_error(PG_ERR_OVERFLOW, "frontier capacity exceeded (SCC iteration %u)", iter);
         if (active == 0) break;
     }
-    PG_CK(cudaMemsetAsync(W.tbl, 0xFF, (size_t)n * sizeof(uint32_t), s));
-    k_scc_min<<<grid, 256, 0, s>>>(n, W.rep, W.tbl);
-    k_scc_label<<<grid, 256, 0, s>>>(n, W.rep, W.tbl, out);
+    PG_CK(cudaMemsetAsync(W.mn, 0xFF, (size_t)n * sizeof(uint32_t), s));
+    k_scc_min<<<grid, 256, 0, s>>>(n, W.rep, W.mn);
+    k_scc_label<<<grid, 256, 0, s>>>(n, W.rep, W.mn, out);
     PG_CK(cudaGetLastError());
     PG_CK(cudaEventRecord(g->ev1, s));
     if (host_out) PG_CK(cudaMemcpyAsync(label_out, out, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
@@ -455,7 +479,7 @@ extern "C" pg_status pg_scc(pg_graph *g, uint32_t *label_out, const pg_config *c
     if (stats) {
         memset(stats, 0, sizeof(*stats));
         stats->rounds = rounds;
-        stats->blocks = blocks;
+        stats->blocks = (uint32_t)g->num_sms;
         stats->threads = threads;
         stats->expansions = expansions;
         float ms = 0.f;
