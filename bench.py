@@ -53,6 +53,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--configs", action="store_true",
+                    help="instead of the headline line: one JSON line per benchmark configuration")
+    ap.add_argument("--with-strip", action="store_true", help="--configs: include the 1 x 20M strip")
     return ap.parse_args()
 
 
@@ -222,10 +225,142 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_configs(args):
+    """One JSON line per benchmark configuration (rank 0, one GPU): every
+    form's device time (CUDA events, min of `steps` after `warmup`), the
+    forms' outputs compared with each other, and the oracle on one host core
+    over a bounded sample (the CPU-baseline leg)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import graphgen as gg
+    import oracle
+    import paper_2404_17101_gb300 as pg
+    torch.cuda.set_device(0)
+    oracle.build()
+    w = pg.trained_weights()
+    steps, warm = max(1, args.steps), max(1, args.warmup)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")
+
+    def best(call, reps=steps, wu=warm):
+        st = pg.Stats()
+        for _ in range(wu):
+            call(st)
+        ts, res = [], None
+        for i in range(reps):
+            flush.fill_(i)
+            res = call(st)
+            ts.append(st.kernel_ms)
+        return min(ts), st, res
+
+    def cpu(fn, budget_s=8.0):
+        t0 = time.perf_counter(); fn(); t = time.perf_counter() - t0
+        reps = max(0, min(4, int(budget_s / max(t, 1e-3)) - 1))
+        ts = [t]
+        for _ in range(reps):
+            t0 = time.perf_counter(); fn(); ts.append(time.perf_counter() - t0)
+        return statistics.median(ts)
+
+    def emit(d):
+        print(json.dumps(d), flush=True)
+
+    def bfs_forms(name, g, extra=None):
+        G = pg.Graph.from_graphgen(g, ell=True)
+        out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        forms = {"tau16": pg.default_config(), "tau64": pg.default_config(tau=64)}
+        if w is not None:
+            G.set_schedule_weights(w)
+            forms["learned"] = pg.default_config(schedule=pg.PG_SCHED_LEARNED)
+        if extra:
+            forms.update(extra)
+        res, ref = {}, None
+        for f, cfg in forms.items():
+            cfg.timeout_ms = 30000
+            reps, wu = (1, 1) if name.startswith("strip") else (steps, warm)
+            ms, st, _ = best(lambda st: G.bfs(0, out=out, cfg=cfg, stats=st), reps, wu)
+            d = pg.to_uint32(out)
+            same = True if ref is None else bool(np.array_equal(d, ref))
+            ref = d if ref is None else ref
+            res[f] = {"ms": ms, "rounds": st.rounds, "same_as_first": same}
+        n_r, m_r = G.count_reached(out)
+        for f in res:
+            res[f]["gteps"] = m_r / res[f]["ms"] / 1e6
+        t_or = cpu(lambda: oracle.bfs(g, 0))
+        emit({"config": name, "kind": "bfs", "n": g.n, "m": g.m, "traversed_edges": m_r, "forms": res,
+              "cpu_oracle": {"ms": t_or * 1e3, "gteps": m_r / t_or / 1e9, "cores": 1}})
+        G.free()
+
+    bfs_forms("C1 grid_1000", gg.grid_1000())
+    bfs_forms("C2 knn_10m", gg.knn_10m())
+
+    # C3: 64 single-source BFS (direction-optimising, plain rounds) vs one batch
+    g = gg.rmat_24()
+    G = pg.Graph.from_graphgen(g)
+    srcs = gg.pick_sources(g, 64, 3)
+    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    c1 = pg.default_config(tau=1, direction=pg.PG_DIR_AUTO)
+    single, m_tot = 0.0, 0
+    for s_ in srcs:
+        ms, _, _ = best(lambda st: G.bfs(int(s_), out=out, cfg=c1, stats=st), 1, 1)
+        single += ms
+        m_tot += G.count_reached(out)[1]
+    D = torch.empty((64, g.n), dtype=torch.int32, device="cuda")
+    cb = pg.default_config(direction=pg.PG_DIR_AUTO)
+    ms_b, st_b, _ = best(lambda st: G.bfs_multi(srcs, cfg=cb, stats=st, out=D))
+    row_ok = bool(np.array_equal(pg.to_uint32(D[17]), pg.to_uint32(G.bfs(int(srcs[17]), cfg=c1))))
+    t_or = cpu(lambda: oracle.bfs(g, int(srcs[0])))
+    emit({"config": "C3 rmat_24", "kind": "bfs x64", "n": g.n, "m": g.m, "traversed_edges_sum": m_tot,
+          "forms": {"single_x64": {"ms": single, "gteps": m_tot / single / 1e6},
+                    "batch64": {"ms": ms_b, "gteps": m_tot / ms_b / 1e6, "rounds": st_b.rounds,
+                                "pull_rounds": st_b.pull_rounds, "row_equals_single": row_ok}},
+          "cpu_oracle": {"ms": 64 * t_or * 1e3, "gteps": m_tot / (64 * t_or) / 1e9, "cores": 1,
+                         "sample": "one source timed, times 64"}})
+    del G, D
+    torch.cuda.empty_cache()
+
+    # C4: 64-source forward + backward reachability in one launch vs 64
+    # single-source launches; then SCC of the same graph
+    g = gg.dgrid_4000()
+    G = pg.Graph.from_graphgen(g, ell=True)
+    srcs = gg.pick_sources(g, 64, 4)
+    both = pg.PG_FWD | pg.PG_BWD
+    ms_d, st_d, _ = best(lambda st: G.reach_multi(srcs, both, cfg=pg.default_config(), stats=st))
+    tuned = G.autotune(srcs, kind=1, direction=both, trials=2)
+    ms_t, st_t, (fw, bw) = best(lambda st: G.reach_multi(srcs, both, cfg=tuned, stats=st))
+    single = 0.0
+    for s_ in srcs[:8]:
+        ms, _, _ = best(lambda st: G.reach_multi([int(s_)], both, cfg=pg.default_config(), stats=st), 1, 1)
+        single += ms
+    single *= 8
+    ms_s, st_s, (lab, it) = best(lambda st: G.scc(cfg=pg.default_config(tau=64), stats=st))
+    ms_s1, _, _ = best(lambda st: G.scc(cfg=pg.default_config(tau=1), stats=st))
+    t_or = cpu(lambda: oracle.reach(g, srcs[:1]), budget_s=4.0)
+    t_scc = cpu(lambda: oracle.scc(g), budget_s=4.0)
+    emit({"config": "C4 dgrid_4000", "kind": "reach fwd+bwd x64, scc", "n": g.n, "m": g.m,
+          "forms": {"batch64_default": {"ms": ms_d, "rounds": st_d.rounds},
+                    "batch64_tuned": {"ms": ms_t, "rounds": st_t.rounds,
+                                      "tau": int(tuned.tau), "chunk": int(tuned.chunk)},
+                    "single_x64": {"ms": single, "sample": "8 sources timed, times 8"},
+                    "scc_tau64": {"ms": ms_s, "iterations": it, "rounds": st_s.rounds},
+                    "scc_tau1": {"ms": ms_s1}},
+          "cpu_oracle": {"reach_ms": 128 * t_or * 1e3, "scc_ms": t_scc * 1e3, "cores": 1,
+                         "sample": "one source, one direction timed, times 128; Tarjan once"}})
+    del G
+    torch.cuda.empty_cache()
+
+    bfs_forms("C5 knn_30m_k3", gg.knn_30m_k3())
+    if args.with_strip:
+        bfs_forms("C5 strip_20m", gg.strip_20m())
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.configs:
+        run_configs(args)
         return
     rank, world, local = dist_env()
     import numpy as np

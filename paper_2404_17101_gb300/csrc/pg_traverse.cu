@@ -574,6 +574,64 @@ __device__ void expand_wave(const TravArgs &A, const Round &R, const WarpSm &S, 
     __syncwarp();
 }
 
+// Padded-row wave with one lane per (entry, slot): 32 / W entries per wave,
+// entry i0 + lane / W reads slot lane % W of its row (W = the widest row of
+// the two directions; a narrower direction leaves its upper slots idle).
+// Each lane relaxes at most one arc and stages at most one child, so a
+// sparse level costs a short path instead of W unrolled slots per lane.
+// Entries whose list is in the CSR (long rows, or a direction without rows)
+// are expanded afterwards, one per lane, by expand_wave.
+template <bool kReach>
+__device__ void expand_rows_sp(const TravArgs &A, const Round &R, const WarpSm &S, Task &T,
+                               const uint32_t *ents, const uint32_t *auxs, uint32_t i0,
+                               uint32_t cnt, uint32_t lw, bool from_bag, int lane, Counters &C) {
+    const uint32_t j = (uint32_t)lane & ((1u << lw) - 1u);
+    const uint32_t i = i0 + ((uint32_t)lane >> lw);
+    const bool valid = i < cnt;
+    uint32_t ent = PG_NONE, aux = 0;
+    if (valid) {
+        ent = PG_DBG_ENTRY(A, ents[i], 8u, kReach);
+        aux = auxs[i];
+    }
+    const bool live = ent != PG_NONE;
+    const uint32_t v = kReach ? (ent & 0x7FFFFFFFu) : ent;
+    const uint32_t dir = kReach ? (ent >> 31) : 0u;
+    const uint32_t *ell = dir ? A.ell1 : A.ell0;
+    const uint32_t Wd = dir ? A.ellw1 : A.ellw0;
+    const bool has_rows = live && ell != nullptr;
+    unsigned long long prop = 0;
+    uint32_t x = PG_NONE;
+    if (live) {
+        prop = (!kReach && !from_bag) ? (unsigned long long)(aux + 1u) : load_prop<kReach>(A, v, dir);
+        if (has_rows && j < Wd) x = __ldg(ell + (size_t)v * Wd + j);
+#ifdef PG_DEBUG_BOUNDS
+        if (x < 0x80000000u) x = PG_DBG_ID(A, x, 9u, false);
+#endif
+    }
+    const bool dead = !kReach && prop == (unsigned long long)PG_INF;
+    const bool lead = live && !dead && j == 0u;
+    const bool is_long = lead && (!has_rows || x == PG_ELL_LONG);
+    const uint32_t caux = kReach ? aux + 1u : (uint32_t)prop;
+    const bool ok_local = eligible<kReach>(R, caux);
+    const bool arc = live && !dead && x < 0x80000000u;
+    const unsigned long long old = relax_issue<kReach>(A, x, dir, prop, arc);
+    if (arc && ok_local) pg_prefetch_l1(ell + (size_t)x * Wd);
+    const bool imp = arc && improved<kReach>(prop, old);
+    if (lead && !is_long) { C.expansions++; C.exp_verts++; }
+    if (arc) C.exp_edges++;
+    stage<kReach>(A, R, S, T, imp, kReach ? (x | (dir << 31)) : x, caux, ok_local, lane, C);
+    // rows kept in the CSR: lane t takes the t-th such entry
+    const unsigned bl = __ballot_sync(kFull, is_long);
+    if (bl) {
+        unsigned mm = bl;
+        for (int q = 0; q < lane && mm; q++) mm &= mm - 1u;
+        const int src = mm ? __ffs(mm) - 1 : 0;
+        const uint32_t e2 = __shfl_sync(kFull, ent, src);
+        const uint32_t a2 = __shfl_sync(kFull, aux, src);
+        expand_wave<kReach>(A, R, S, T, mm ? e2 : PG_NONE, a2, from_bag, lane, C);
+    }
+}
+
 // One warp task: c frontier entries plus the local search they start.
 template <bool kReach>
 __device__ void run_task(const TravArgs &A, const Round &R, const WarpSm &S, uint32_t entry,
@@ -610,6 +668,9 @@ __device__ void cta_round(const TravArgs &A, const Round &R, const WarpSm &S, co
                           int lane, int wib, int nwib, Counters &C) {
     const uint32_t nb = gridDim.x;
     const uint32_t QC = A.L.cta_queue;
+    // slot-parallel waves when padded rows exist: log2 of the widest row
+    const uint32_t wmax = max(A.ellw0, A.ellw1);
+    const uint32_t lw = wmax >= 16u ? 4u : (wmax >= 8u ? 3u : (wmax >= 4u ? 2u : 0u));
     uint32_t cc = (R.F + nb - 1) / nb;
     cc = max(1u, min(cc, QC / 2));
     const uint32_t span = nb * cc;
@@ -641,11 +702,17 @@ __device__ void cta_round(const TravArgs &A, const Round &R, const WarpSm &S, co
             T.cta_aux = Q.aux[nl];
             T.cta_n = &Q.n[nl];
             T.cta_cap = QC;
-            for (uint32_t w0 = (uint32_t)wib * 32u; w0 < ncur; w0 += (uint32_t)nwib * 32u) {
-                const uint32_t i = w0 + lane;
-                const uint32_t e = (i < ncur) ? Q.ent[cl][i] : PG_NONE;
-                const uint32_t ax = (i < ncur) ? Q.aux[cl][i] : 0u;
-                expand_wave<kReach>(A, R, S, T, e, ax, h == 0, lane, C);
+            if (lw) {
+                const uint32_t G = 32u >> lw;  // entries per slot-parallel wave
+                for (uint32_t w0 = (uint32_t)wib * G; w0 < ncur; w0 += (uint32_t)nwib * G)
+                    expand_rows_sp<kReach>(A, R, S, T, Q.ent[cl], Q.aux[cl], w0, ncur, lw, h == 0, lane, C);
+            } else {
+                for (uint32_t w0 = (uint32_t)wib * 32u; w0 < ncur; w0 += (uint32_t)nwib * 32u) {
+                    const uint32_t i = w0 + lane;
+                    const uint32_t e = (i < ncur) ? Q.ent[cl][i] : PG_NONE;
+                    const uint32_t ax = (i < ncur) ? Q.aux[cl][i] : 0u;
+                    expand_wave<kReach>(A, R, S, T, e, ax, h == 0, lane, C);
+                }
             }
             if (threadIdx.x == 0) Q.n[ql] = 0;
             __syncthreads();
