@@ -894,7 +894,14 @@ __device__ __forceinline__ uint32_t mix32(uint32_t a, uint32_t b) {
 
 // Schedule-MLP inference on one warp; weights in shared memory.  Returns
 // the arg-max action among the allowed ones (ties -> lowest index).
-__device__ uint32_t mlp_decide(const float *W, const float (&x)[5], bool allow_pull, int lane) {
+// The network's choice, judged against the fixed-tau push action a_fix: the
+// network overrides it only when its predicted gain (standardised log2
+// kernel-time units) exceeds kJudgeMargin, so near-ties keep the fixed
+// heuristic.
+constexpr float kJudgeMargin = 0.1f;
+
+__device__ uint32_t mlp_decide(const float *W, const float (&x)[5], bool allow_pull, uint32_t a_fix,
+                               int lane) {
     const float *W1 = W, *b1 = W + 160, *W2 = W + 192, *b2 = W + 1216, *W3 = W + 1248,
                 *b3 = W + 1504;
     float h1 = b1[lane];
@@ -916,7 +923,8 @@ __device__ uint32_t mlp_decide(const float *W, const float (&x)[5], bool allow_p
         if ((uint32_t)t == PG_ACTION_PULL && !allow_pull) continue;
         if (yt > by) { by = yt; best = (uint32_t)t; }
     }
-    return best;
+    const float yf = __shfl_sync(kFull, y, (int)a_fix);
+    return (by - yf > kJudgeMargin) ? best : a_fix;
 }
 
 __device__ __forceinline__ float flog2p1(float x) { return log2f(1.0f + x); }
@@ -1077,7 +1085,9 @@ __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
         uint32_t action;
         if (A.L.schedule == PG_SCHED_LEARNED) {
             if (wib == 0) {
-                const uint32_t a = mlp_decide(s_w, x, can_pull, lane);
+                // the fixed schedule's push action: tau = 2^a_fix (rounded down, at most 64)
+                const uint32_t a_fix = min(31u - (uint32_t)__clz((int)max(A.L.tau, 1u)), 6u);
+                const uint32_t a = mlp_decide(s_w, x, can_pull, a_fix, lane);
                 if (lane == 0) s_action = a;
             }
             __syncthreads();
