@@ -60,10 +60,12 @@ def _load():
         lib.gg_from_arcs.argtypes = [u32, u32, ctypes.c_void_p, ctypes.c_void_p, i32, i32, P(_CSR)]
         lib.gg_pick_sources.argtypes = [u32, ctypes.c_void_p, u32, u64, ctypes.c_void_p]
         lib.gg_free.argtypes = [P(_CSR)]
+        lib.gg_read_adj.argtypes = [ctypes.c_char_p, P(_CSR)]
+        lib.gg_write_adj.argtypes = [ctypes.c_char_p, u32, u32, ctypes.c_void_p, ctypes.c_void_p]
         lib.gg_rand.argtypes = [u64, u64, u64]
         lib.gg_rand.restype = u64
         for f in ("gg_grid", "gg_dgrid", "gg_knn", "gg_rmat", "gg_random", "gg_from_arcs",
-                  "gg_pick_sources", "gg_num_threads"):
+                  "gg_pick_sources", "gg_num_threads", "gg_read_adj", "gg_write_adj"):
             getattr(lib, f).restype = i32
         _lib = lib
     return _lib
@@ -163,6 +165,23 @@ def from_arcs(n: int, src, dst, symmetrize: bool = False, clean: bool = True,
     _check(_load().gg_from_arcs(n, len(s), s.ctypes.data, d.ctypes.data, int(symmetrize),
                                 int(clean), ctypes.byref(c)), "from_arcs")
     return _take(c, directed and not symmetrize, "arcs")
+
+
+def read_adj(path: str, directed: bool = True) -> Graph:
+    """Read a graph in the PBBS "AdjacencyGraph" text format (header, n, m,
+    n offsets, m targets).  Arcs are taken as given; `directed=False` marks a
+    file that stores both directions of every edge."""
+    c = _CSR()
+    _check(_load().gg_read_adj(os.fsencode(path), ctypes.byref(c)), f"read_adj({path})")
+    return _take(c, directed, os.path.basename(path), path=path)
+
+
+def write_adj(g: Graph, path: str) -> None:
+    """Write g in the PBBS "AdjacencyGraph" text format."""
+    off = np.ascontiguousarray(g.offsets, dtype=np.uint32)
+    idx = np.ascontiguousarray(g.indices, dtype=np.uint32)
+    _check(_load().gg_write_adj(os.fsencode(path), g.n, g.m, off.ctypes.data, idx.ctypes.data),
+           f"write_adj({path})")
 
 
 def pick_sources(g: Graph, k: int, seed: int) -> np.ndarray:

@@ -26,6 +26,7 @@
  *   gg_random tiny uniform random graphs for brute-force checks
  */
 #include <stdint.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
@@ -483,4 +484,69 @@ int gg_num_threads(void) {
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------ file input -- */
+/* The PBBS "AdjacencyGraph" text format (the problem-based benchmark
+ * suite's graph format, also read by GBBS): the header line
+ * "AdjacencyGraph", then n, m, the n offsets and the m targets, one
+ * decimal number per line (any whitespace separates).  The graph is read
+ * as given (arcs u -> indices[...]); lists are not re-sorted or deduplicated. */
+
+#define GG_ERR_IO 4
+#define GG_ERR_FORMAT 5
+
+static int read_u64(FILE *f, uint64_t *x) {
+    int c;
+    do { c = fgetc(f); } while (c == ' ' || c == '\n' || c == '\r' || c == '\t');
+    if (c < '0' || c > '9') return -1;
+    uint64_t v = 0;
+    while (c >= '0' && c <= '9') {
+        v = v * 10u + (uint64_t)(c - '0');
+        if (v > 0xFFFFFFFFull) return -1;
+        c = fgetc(f);
+    }
+    *x = v;
+    return 0;
+}
+
+int gg_read_adj(const char *path, gg_csr *out) {
+    if (!path || !out) return GG_ERR_ARG;
+    memset(out, 0, sizeof(*out));
+    FILE *f = fopen(path, "rb");
+    if (!f) return GG_ERR_IO;
+    char head[32] = {0};
+    if (fscanf(f, "%31s", head) != 1 || strcmp(head, "AdjacencyGraph") != 0) { fclose(f); return GG_ERR_FORMAT; }
+    uint64_t n = 0, m = 0;
+    if (read_u64(f, &n) || read_u64(f, &m) || n == 0 || n >= 0x80000000ull) { fclose(f); return GG_ERR_FORMAT; }
+    uint32_t *off = (uint32_t *)malloc(((size_t)n + 1) * sizeof(uint32_t));
+    uint32_t *idx = (uint32_t *)malloc((size_t)(m ? m : 1) * sizeof(uint32_t));
+    if (!off || !idx) { free(off); free(idx); fclose(f); return GG_ERR_OOM; }
+    int bad = 0;
+    for (uint64_t v = 0; v < n && !bad; v++) {
+        uint64_t x;
+        if (read_u64(f, &x) || x > m || (v == 0 && x != 0) || (v > 0 && x < off[v - 1])) bad = 1;
+        else off[v] = (uint32_t)x;
+    }
+    off[n] = (uint32_t)m;
+    for (uint64_t e = 0; e < m && !bad; e++) {
+        uint64_t x;
+        if (read_u64(f, &x) || x >= n) bad = 1;
+        else idx[e] = (uint32_t)x;
+    }
+    fclose(f);
+    if (bad) { free(off); free(idx); return GG_ERR_FORMAT; }
+    out->n = (uint32_t)n; out->m = (uint32_t)m; out->offsets = off; out->indices = idx;
+    return GG_OK;
+}
+
+int gg_write_adj(const char *path, uint32_t n, uint32_t m, const uint32_t *offsets, const uint32_t *indices) {
+    if (!path || !offsets || (m && !indices)) return GG_ERR_ARG;
+    FILE *f = fopen(path, "wb");
+    if (!f) return GG_ERR_IO;
+    int ok = fprintf(f, "AdjacencyGraph\n%u\n%u\n", n, m) > 0;
+    for (uint32_t v = 0; v < n && ok; v++) ok = fprintf(f, "%u\n", offsets[v]) > 0;
+    for (uint32_t e = 0; e < m && ok; e++) ok = fprintf(f, "%u\n", indices[e]) > 0;
+    if (fclose(f) != 0) ok = 0;
+    return ok ? GG_OK : GG_ERR_IO;
 }

@@ -896,9 +896,11 @@ __device__ __forceinline__ uint32_t mix32(uint32_t a, uint32_t b) {
 // the arg-max action among the allowed ones (ties -> lowest index).
 // The network's choice, judged against the fixed-tau push action a_fix: the
 // network overrides it only when its predicted gain (standardised log2
-// kernel-time units) exceeds kJudgeMargin, so near-ties keep the fixed
-// heuristic.
-constexpr float kJudgeMargin = 0.1f;
+// kernel-time units) exceeds a margin, so near-ties keep the fixed heuristic.
+// Raising tau or pulling needs kJudgeUp; lowering tau, which adds rounds,
+// needs the stronger evidence kJudgeDown.
+constexpr float kJudgeUp = 0.1f;
+constexpr float kJudgeDown = 0.3f;
 
 __device__ uint32_t mlp_decide(const float *W, const float (&x)[5], bool allow_pull, uint32_t a_fix,
                                int lane) {
@@ -924,7 +926,7 @@ __device__ uint32_t mlp_decide(const float *W, const float (&x)[5], bool allow_p
         if (yt > by) { by = yt; best = (uint32_t)t; }
     }
     const float yf = __shfl_sync(kFull, y, (int)a_fix);
-    return (by - yf > kJudgeMargin) ? best : a_fix;
+    return (by - yf > (best < a_fix ? kJudgeDown : kJudgeUp)) ? best : a_fix;
 }
 
 __device__ __forceinline__ float flog2p1(float x) { return log2f(1.0f + x); }

@@ -68,8 +68,8 @@ def test_adam_matches_oracle(pg):
     assert _close(M.cpu().numpy(), mw, rtol=1e-5, atol_rel=1e-6)
 
 
-JUDGE_MARGIN = 0.1  # the kernel's margin for overriding the fixed-tau action
-A_FIX = 4           # push with the default tau = 16
+JUDGE_UP, JUDGE_DOWN = 0.1, 0.3  # the kernel's margins for overriding the fixed-tau action
+A_FIX = 4                        # push with the default tau = 16
 
 
 def test_in_loop_decision_matches_oracle_argmax(pg):
@@ -100,9 +100,10 @@ def test_in_loop_decision_matches_oracle_argmax(pg):
             if Y[r, order[0]] - Y[r, order[1]] < 1e-4:
                 continue
             gain = Y[r, order[0]] - Y[r, A_FIX]
-            if abs(gain - JUDGE_MARGIN) < 1e-4:
+            margin = JUDGE_DOWN if order[0] < A_FIX else JUDGE_UP
+            if abs(gain - margin) < 1e-4:
                 continue
-            want = order[0] if gain > JUDGE_MARGIN else A_FIX
+            want = order[0] if gain > margin else A_FIX
             assert acts[r] == want, (trial, r, acts[r], order[:3], Y[r])
 
 

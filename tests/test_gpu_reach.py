@@ -120,3 +120,36 @@ def test_bfs_multi_heavy_directed(pg):
     G.set_transpose(toff, tidx)
     D = pg.to_uint32(G.bfs_multi(srcs, cfg=pg.default_config(direction=1)))
     assert np.array_equal(D, want)
+
+
+def _ell_width(deg):
+    """The library's padded-row width rule: the smallest of 4 / 8 / 16 that
+    all but 0.1% of the vertices fit (0: no padded rows)."""
+    tol = len(deg) // 1000
+    for w in (4, 8, 16):
+        if int((deg > w).sum()) <= tol:
+            return w
+    return 0
+
+
+def test_padded_rows_of_different_widths(pg):
+    """Forward rows 4 wide, reverse rows 8 wide: slot-parallel waves group
+    lanes by the wider row and each direction uses its own width."""
+    rng = np.random.default_rng(21)
+    n = 50_000
+    src = np.repeat(np.arange(n), 2)
+    dst = rng.integers(0, n, 2 * n)
+    g = gg.from_arcs(n, src, dst, directed=True)
+    toff, _ = oracle.transpose(g)
+    assert _ell_width(np.diff(g.offsets.astype(np.int64))) == 4
+    assert _ell_width(np.diff(toff.astype(np.int64))) == 8
+    G = pg.Graph.from_graphgen(g, ell=True)
+    srcs = gg.pick_sources(g, 64, 8)
+    want_f, want_b = oracle.reach(g, srcs), oracle.reach(g, srcs, backward=True)
+    for tau in (1, 4, 16, 64):
+        f, b = _reach(pg, G, srcs, pg.PG_FWD | pg.PG_BWD, tau=tau)
+        assert np.array_equal(f, want_f), tau
+        assert np.array_equal(b, want_b), tau
+    for s_ in srcs[:4]:
+        d = pg.to_uint32(G.bfs(int(s_), cfg=pg.default_config(tau=16)))
+        assert np.array_equal(d, oracle.bfs(g, int(s_)))

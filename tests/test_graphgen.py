@@ -1,5 +1,6 @@
 """Generator checks (no GPU): structure, determinism and exact kNN."""
 import numpy as np
+import pytest
 
 import graphgen as gg
 
@@ -91,3 +92,26 @@ def test_pick_sources():
 def test_rand_is_counter_based():
     assert gg.rand(1, 2, 3) == gg.rand(1, 2, 3)
     assert len({gg.rand(1, 2, i) for i in range(1000)}) == 1000
+
+
+def test_adjacency_graph_file_round_trip(tmp_path):
+    """PBBS AdjacencyGraph text files: write then read gives the same CSR,
+    a hand-written file parses to the expected arcs, and malformed files
+    (wrong header, decreasing offsets, a target >= n, truncation) are
+    rejected."""
+    g = gg.dgrid(20, 30, 5, shortcuts=7)
+    p = str(tmp_path / "g.adj")
+    gg.write_adj(g, p)
+    h = gg.read_adj(p)
+    assert (h.n, h.m) == (g.n, g.m)
+    assert np.array_equal(h.offsets, g.offsets) and np.array_equal(h.indices, g.indices)
+    q = tmp_path / "tiny.adj"
+    q.write_text("AdjacencyGraph\n3\n4\n0\n2\n3\n1\n2\n2\n0\n")
+    t = gg.read_adj(str(q))
+    assert t.offsets.tolist() == [0, 2, 3, 4] and t.indices.tolist() == [1, 2, 2, 0]
+    for bad in ("WeightedAdjacencyGraph\n1\n0\n0\n", "AdjacencyGraph\n3\n2\n0\n2\n1\n0\n1\n",
+                "AdjacencyGraph\n2\n1\n0\n1\n5\n", "AdjacencyGraph\n3\n4\n0\n2\n"):
+        b = tmp_path / "bad.adj"
+        b.write_text(bad)
+        with pytest.raises(RuntimeError):
+            gg.read_adj(str(b))
