@@ -101,11 +101,14 @@ def adam_step(p, g, m, v, t: int, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
     return p - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
+ROUND_CAP = 2.0 ** 14  # the round-index feature saturates here (the training range)
+
+
 def features(frontier, out_edges, rnd, prev_ns) -> np.ndarray:
     """Feature rows from raw per-round statistics (arrays of equal length)."""
     Fz = np.asarray(frontier, dtype=np.float64)
     E = np.asarray(out_edges, dtype=np.float64)
-    r = np.asarray(rnd, dtype=np.float64)
+    r = np.minimum(np.asarray(rnd, dtype=np.float64), ROUND_CAP)
     tp = np.asarray(prev_ns, dtype=np.float64) / 1000.0
     mean = np.where(Fz > 0, E / np.maximum(Fz, 1.0), 0.0)
     return np.stack([np.log2(1 + Fz) / 24, np.log2(1 + E) / 32, np.log2(1 + mean) / 8,

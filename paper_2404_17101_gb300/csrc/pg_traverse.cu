@@ -931,6 +931,11 @@ __device__ uint32_t mlp_decide(const float *W, const float (&x)[5], bool allow_p
 
 __device__ __forceinline__ float flog2p1(float x) { return log2f(1.0f + x); }
 
+// The round-index feature saturates at 2^14 rounds: the training states never
+// go further (strips are sampled up to about 17k rounds), and the network is
+// not evaluated outside that range.
+constexpr uint32_t kRoundFeatureCap = 1u << 14;
+
 template <bool kReach>
 __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1078,7 +1083,7 @@ __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
             x[0] = flog2p1((float)R.F) / 24.f;
             x[1] = flog2p1((float)E) / 32.f;
             x[2] = flog2p1((float)E / (float)R.F) / 8.f;
-            x[3] = flog2p1((float)r) / 24.f;
+            x[3] = flog2p1((float)min(r, kRoundFeatureCap)) / 24.f;
             x[4] = flog2p1((float)prev_ns * 1e-3f) / 16.f;
         }
 

@@ -95,3 +95,6 @@ def test_features_closed_form():
     assert np.allclose(X[0], [1 / 24, 2 / 32, 2 ** 0 * np.log2(4) / 8, 0, 1 / 16])
     assert np.allclose(X[1], [0, 0, 0, 1 / 24, 0])
     assert np.allclose(X[2], [2 / 24, np.log2(22) / 32, 3 / 8, 2 / 24, 2 / 16])
+    # the round index saturates at 2^14 rounds (log2(1 + 2^14) / 24)
+    Y = mlp.features([1, 1], [2, 2], [2 ** 14, 10 ** 7], [0, 0])
+    assert np.isclose(Y[0, 3], np.log2(1 + 2 ** 14) / 24) and Y[1, 3] == Y[0, 3]
