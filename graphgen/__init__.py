@@ -10,7 +10,7 @@ appendix graph table): synthetic grids (REC/SREC), k-nearest-neighbour
 graphs (CH5/GL5/COS5), road-like large-diameter graphs and R-MAT stand-ins
 for the social/web low-diameter graphs.  The named workloads at the bottom
 (`grid_1000`, `knn_10m`, `rmat_24`, `dgrid_4000`, `knn_30m_k3`,
-`strip_20m`) are the five benchmark configurations described in the design doc.
+`strip_20m`) are the five benchmark configurations.
 """
 from __future__ import annotations
 
@@ -201,7 +201,7 @@ def num_threads() -> int:
 
 
 # ------------------------------------------------------------------ workloads
-# The benchmark configurations (sizes and seeds as in the design doc).
+# The benchmark configurations (sizes and seeds).
 
 def grid_1000() -> Graph:
     """1000 x 1000 undirected 4-neighbour grid, source 0 (REC-like)."""

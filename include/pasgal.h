@@ -100,7 +100,8 @@ typedef struct pg_round_trace {
 typedef struct pg_config {
     uint32_t struct_size;       /* sizeof(pg_config) */
     uint32_t schedule;          /* PG_SCHED_* */
-    uint32_t tau;               /* VGC budget: vertices a task may visit per frontier vertex (1 = plain BFS) */
+    uint32_t tau;               /* VGC window: a task's local search expands vertices within tau hops of the
+                                   round's frontier (BFS: distance < L + tau; reach: hops < tau); 1 = plain BFS */
     uint32_t direction;         /* PG_DIR_PUSH or PG_DIR_AUTO (fixed schedule only) */
     uint32_t alpha;             /* push -> pull when out_edges(F) > unexplored_edges / alpha */
     uint32_t beta;              /* pull -> push when |F| < n / beta */

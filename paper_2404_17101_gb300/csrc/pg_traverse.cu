@@ -6,12 +6,16 @@
 //   REACH (Sec. 2.1): value = uint64 source bitmask, relax = atomicOr(mask),
 //                     forward (G) and backward (G^T) searches share the rounds.
 //
-// Vertical granularity control (Sec. 2.1) on the GPU is a per-warp tau-hop
-// local search: a warp takes a chunk of frontier entries and keeps expanding
-// the vertices it improves, from a shared-memory FIFO, as long as they lie
-// within tau hops of the round's frontier (BFS: new distance < L + tau,
-// L = smallest distance in the frontier; REACH: hop count < tau) and a
-// per-task budget lasts; other improvements spill to the next frontier bag.
+// Vertical granularity control (Sec. 2.1) on the GPU is a tau-hop local
+// search: a task keeps expanding the vertices it improves as long as they
+// lie within tau hops of the round's frontier (BFS: new distance < L + tau,
+// L = smallest distance in the frontier; REACH: hop count < tau); other
+// improvements spill to the next frontier bag.  By default (PG_VGC_CTA) a
+// task is a CTA's share of the bag, searched level by level in shared
+// memory with all warps splitting each level; with padded rows a level is
+// cut into slot-parallel waves (one lane per vertex and row slot).  The
+// alternative (PG_VGC_WARP) is a warp's chunk of entries with a
+// shared-memory FIFO and a per-task budget.
 // A vertex whose value improves is always expanded again later (Sec. 2.2:
 // a vertex can be visited multiple times), so the result is the exact
 // fixpoint for every tau and every push/pull sequence.
@@ -904,7 +908,9 @@ constexpr float kJudgeDown = 0.3f;
 
 __device__ uint32_t mlp_decide(const float *W, const float (&x)[5], bool allow_pull, uint32_t a_fix,
                                int lane) {
-    const float *W1 = W, *b1 = W + 160, *W2 = W + 192, *b2 = W + 1216, *W3 = W + 1248,
+    // packed order W1 (32 x 5), b1, W2 (32 x 32), b2, W3 (8 x 32), b3; W2 and
+    // W3 were stored transposed when the CTA loaded them
+    const float *W1 = W, *b1 = W + 160, *W2t = W + 192, *b2 = W + 1216, *W3t = W + 1248,
                 *b3 = W + 1504;
     float h1 = b1[lane];
 #pragma unroll
@@ -912,12 +918,12 @@ __device__ uint32_t mlp_decide(const float *W, const float (&x)[5], bool allow_p
     h1 = fmaxf(h1, 0.f);
     float h2 = b2[lane];
 #pragma unroll
-    for (int i = 0; i < 32; i++) h2 = fmaf(W2[lane * 32 + i], __shfl_sync(kFull, h1, i), h2);
+    for (int i = 0; i < 32; i++) h2 = fmaf(W2t[i * 32 + lane], __shfl_sync(kFull, h1, i), h2);
     h2 = fmaxf(h2, 0.f);
     const int a = lane & 7;
     float y = b3[a];
 #pragma unroll
-    for (int i = 0; i < 32; i++) y = fmaf(W3[a * 32 + i], __shfl_sync(kFull, h2, i), y);
+    for (int i = 0; i < 32; i++) y = fmaf(W3t[i * 8 + a], __shfl_sync(kFull, h2, i), y);
     uint32_t best = 0;
     float by = __shfl_sync(kFull, y, 0);
     for (int t = 1; t < (int)PG_NUM_ACTIONS; t++) {
@@ -977,7 +983,14 @@ __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
     }
 
     if (A.L.schedule == PG_SCHED_LEARNED)
-        for (int i = threadIdx.x; i < (int)PG_MLP_NPARAMS; i += blockDim.x) s_w[i] = A.L.weights[i];
+        for (int i = threadIdx.x; i < (int)PG_MLP_NPARAMS; i += blockDim.x) {
+            // W2 (32 x 32) and W3 (8 x 32) are stored transposed, so that in
+            // mlp_decide the lanes read consecutive words (no bank conflicts)
+            int j = i;
+            if (i >= 192 && i < 1216) j = 192 + ((i - 192) & 31) * 32 + (i - 192) / 32;
+            else if (i >= 1248 && i < 1504) j = 1248 + ((i - 1248) & 31) * 8 + (i - 1248) / 32;
+            s_w[j] = A.L.weights[i];
+        }
 
     PgCtrl *ctrl = A.ctrl;
     unsigned gen = 0;
