@@ -5,7 +5,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <vector>
 
 #include "pg_internal.cuh"
 
@@ -63,7 +65,70 @@ extern "C" void pg_config_default(pg_config *c) {
     c->test_stall_block = 0xFFFFFFFFu;
 }
 
-pg_status pg_resolve_config(pg_graph *g, const pg_config *cfg, PgLaunch *L) {
+// ------------------------------------------------------------ graph memory
+// A graph's device buffers come from the device's default memory pool in
+// stream order (cudaMallocAsync).  The pool keeps up to kPoolKeepBytes of
+// freed memory for reuse (set once per device, for this process), so
+// uploading and freeing graphs repeatedly costs no driver allocation.  A
+// buffer is only freed once the device is idle: pg_graph_free and the
+// replacement paths synchronise first.
+constexpr uint64_t kPoolKeepBytes = 8ull << 30;
+constexpr int kMaxPoolDevices = 64;
+static std::mutex g_pool_mu;
+static bool g_pool_ready[kMaxPoolDevices];
+
+static void pool_setup(int dev) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (dev < 0 || dev >= kMaxPoolDevices || g_pool_ready[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = kPoolKeepBytes;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();  // a device without pools keeps the driver default
+    g_pool_ready[dev] = true;
+}
+
+static cudaError_t dev_alloc(void *p, size_t bytes, cudaStream_t s) {
+    return cudaMallocAsync(reinterpret_cast<void **>(p), bytes, s);
+}
+
+// Replace a buffer in use by earlier calls: wait for the device, then free.
+static void dev_free_idle(void *p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    cudaFreeAsync(p, 0);
+}
+
+// Pinned host copies of the control block: a process-wide free list
+// (cudaMallocHost is slow enough to show in an upload).
+static std::mutex g_pin_mu;
+static std::vector<PgCtrl *> g_pin_free;
+
+static PgCtrl *pinned_ctrl_get() {
+    {
+        std::lock_guard<std::mutex> lk(g_pin_mu);
+        if (!g_pin_free.empty()) {
+            PgCtrl *p = g_pin_free.back();
+            g_pin_free.pop_back();
+            return p;
+        }
+    }
+    PgCtrl *p = nullptr;
+    if (cudaMallocHost(&p, sizeof(PgCtrl)) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+static void pinned_ctrl_put(PgCtrl *p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.push_back(p);
+}
+
+pg_status pg_resolve_config(pg_graph *g, const pg_config *cfg, PgLaunch *L, cudaStream_t s) {
     pg_config d;
     pg_config_default(&d);
     const pg_config *c = cfg ? cfg : &d;
@@ -93,8 +158,8 @@ pg_status pg_resolve_config(pg_graph *g, const pg_config *cfg, PgLaunch *L) {
         // more vertices qualify as hubs: grow the hub lists (2 bags x 2 directions)
         PgHub *h = nullptr;
         const uint32_t cap = 2 * (g->m / L->hub_degree) + 66;
-        PG_CK(cudaMalloc(&h, (size_t)2 * cap * sizeof(PgHub)));
-        cudaFree(g->d_hubs);
+        PG_CK(dev_alloc(&h, (size_t)2 * cap * sizeof(PgHub), s));
+        dev_free_idle(g->d_hubs);
         g->d_hubs = h;
         g->hub_cap = cap;
         g->hub_degree_alloc = L->hub_degree;
@@ -114,13 +179,14 @@ pg_status pg_resolve_config(pg_graph *g, const pg_config *cfg, PgLaunch *L) {
         if (!c->script || c->script_len == 0)
             return pg_set_error(PG_ERR_INVALID_ARG, "PG_SCHED_SCRIPT needs script and script_len");
         if (c->script_len > g->script_cap) {
-            if (g->d_script) cudaFree(g->d_script);
+            dev_free_idle(g->d_script);
             g->d_script = nullptr;
             g->script_cap = 0;
-            PG_CK(cudaMalloc(&g->d_script, c->script_len));
+            PG_CK(dev_alloc(&g->d_script, c->script_len, s));
             g->script_cap = c->script_len;
         }
-        PG_CK(cudaMemcpy(g->d_script, c->script, c->script_len, cudaMemcpyHostToDevice));
+        PG_CK(cudaMemcpyAsync(g->d_script, c->script, c->script_len, cudaMemcpyHostToDevice, s));
+        PG_CK(cudaStreamSynchronize(s));
         L->script = g->d_script;
         L->script_len = c->script_len;
     }
@@ -131,10 +197,10 @@ pg_status pg_resolve_config(pg_graph *g, const pg_config *cfg, PgLaunch *L) {
     }
     if (c->trace_out && c->trace_cap) {
         if (c->trace_cap > g->trace_cap) {
-            if (g->d_trace) cudaFree(g->d_trace);
+            dev_free_idle(g->d_trace);
             g->d_trace = nullptr;
             g->trace_cap = 0;
-            PG_CK(cudaMalloc(&g->d_trace, (size_t)c->trace_cap * sizeof(pg_round_trace)));
+            PG_CK(dev_alloc(&g->d_trace, (size_t)c->trace_cap * sizeof(pg_round_trace), s));
             g->trace_cap = c->trace_cap;
         }
         L->trace = g->d_trace;
@@ -143,12 +209,12 @@ pg_status pg_resolve_config(pg_graph *g, const pg_config *cfg, PgLaunch *L) {
     return PG_OK;
 }
 
-pg_status pg_stage(pg_graph *g, size_t bytes, void **dev) {
+pg_status pg_stage(pg_graph *g, size_t bytes, void **dev, cudaStream_t s) {
     if (bytes > g->stage_bytes) {
-        if (g->d_stage) cudaFree(g->d_stage);
+        dev_free_idle(g->d_stage);
         g->d_stage = nullptr;
         g->stage_bytes = 0;
-        PG_CK(cudaMalloc(&g->d_stage, bytes));
+        PG_CK(dev_alloc(&g->d_stage, bytes, s));
         g->stage_bytes = bytes;
     }
     *dev = g->d_stage;
@@ -338,7 +404,7 @@ static pg_status build_rows(pg_graph *g, int which, bool allow, cudaStream_t s) 
     else if (h[2] <= tol) W = 16;
     if (!W) return PG_OK;
     uint32_t *ell = nullptr;
-    if (cudaMalloc(&ell, (size_t)g->n * W * sizeof(uint32_t)) != cudaSuccess) {
+    if (dev_alloc(&ell, (size_t)g->n * W * sizeof(uint32_t), s) != cudaSuccess) {
         cudaGetLastError();  // no room: CSR only
         return PG_OK;
     }
@@ -376,23 +442,25 @@ static pg_status validate(pg_graph *g, const uint32_t *off, const uint32_t *idx,
 
 static void release(pg_graph *g) {
     if (!g) return;
-    if (g->d_ell[1] && g->d_ell[1] != g->d_ell[0]) cudaFree(g->d_ell[1]);
-    cudaFree(g->d_ell[0]);
-    cudaFree(g->d_off);
-    cudaFree(g->d_idx);
+    cudaDeviceSynchronize();  // no call may still use the buffers
+    auto fr = [](void *p) { if (p) cudaFreeAsync(p, 0); };
+    if (g->d_ell[1] && g->d_ell[1] != g->d_ell[0]) fr(g->d_ell[1]);
+    fr(g->d_ell[0]);
+    fr(g->d_off);
+    fr(g->d_idx);
     if (!g->transpose_is_self) {
-        cudaFree(g->d_toff);
-        cudaFree(g->d_tidx);
+        fr(g->d_toff);
+        fr(g->d_tidx);
     }
-    cudaFree(g->d_bag);
-    cudaFree(g->d_stamp);
-    cudaFree(g->d_hubs);
-    cudaFree(g->d_ctrl);
-    if (g->h_ctrl) cudaFreeHost(g->h_ctrl);
-    cudaFree(g->d_stage);
-    cudaFree(g->d_trace);
-    cudaFree(g->d_script);
-    cudaFree(g->d_weights);
+    fr(g->d_bag);
+    fr(g->d_stamp);
+    fr(g->d_hubs);
+    fr(g->d_ctrl);
+    pinned_ctrl_put(g->h_ctrl);
+    fr(g->d_stage);
+    fr(g->d_trace);
+    fr(g->d_script);
+    fr(g->d_weights);
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
     pg_msbfs_release(g);
@@ -403,14 +471,15 @@ static void release(pg_graph *g) {
 static pg_status alloc_workspace(pg_graph *g, uint32_t hub_degree, cudaStream_t s) {
     const uint32_t n = g->n;
     g->bag_cap = 2 * n + 64;  // REACH holds forward and backward entries
-    PG_CK(cudaMalloc(&g->d_bag, (size_t)2 * g->bag_cap * sizeof(uint32_t)));
-    PG_CK(cudaMalloc(&g->d_stamp, (size_t)2 * n * sizeof(uint32_t)));
+    PG_CK(dev_alloc(&g->d_bag, (size_t)2 * g->bag_cap * sizeof(uint32_t), s));
+    PG_CK(dev_alloc(&g->d_stamp, (size_t)2 * n * sizeof(uint32_t), s));
     PG_CK(cudaMemsetAsync(g->d_stamp, 0, (size_t)2 * n * sizeof(uint32_t), s));
     g->hub_degree_alloc = hub_degree;
     g->hub_cap = 2 * (g->m / hub_degree) + 66;
-    PG_CK(cudaMalloc(&g->d_hubs, (size_t)2 * g->hub_cap * sizeof(PgHub)));
-    PG_CK(cudaMalloc(&g->d_ctrl, sizeof(PgCtrl)));
-    PG_CK(cudaMallocHost(&g->h_ctrl, sizeof(PgCtrl)));
+    PG_CK(dev_alloc(&g->d_hubs, (size_t)2 * g->hub_cap * sizeof(PgHub), s));
+    PG_CK(dev_alloc(&g->d_ctrl, sizeof(PgCtrl), s));
+    g->h_ctrl = pinned_ctrl_get();
+    if (!g->h_ctrl) return pg_set_error(PG_ERR_OOM, "pinned host status buffer");
     g->epoch = 1;
     return PG_OK;
 }
@@ -439,8 +508,9 @@ extern "C" pg_status pg_graph_upload(const uint32_t *offsets, const uint32_t *in
     } while (0)
 #define PG_TRYC(call) PG_TRY(((call) == cudaSuccess) ? PG_OK : pg_cuda_error(cudaGetLastError(), #call))
     {
-        cudaError_t e = cudaMalloc(&g->d_off, ((size_t)n + 1) * sizeof(uint32_t));
-        if (e == cudaSuccess) e = cudaMalloc(&g->d_idx, (size_t)(m ? m : 1) * sizeof(uint32_t));
+        pool_setup(dev);
+        cudaError_t e = dev_alloc(&g->d_off, ((size_t)n + 1) * sizeof(uint32_t), s);
+        if (e == cudaSuccess) e = dev_alloc(&g->d_idx, (size_t)(m ? m : 1) * sizeof(uint32_t), s);
         if (e != cudaSuccess) { release(g); return pg_cuda_error(e, "cudaMalloc(graph)"); }
     }
     PG_TRY(copy_in(g->d_off, offsets, (size_t)n + 1, s));
@@ -486,17 +556,18 @@ extern "C" pg_status pg_graph_set_transpose(pg_graph *g, const uint32_t *t_offse
     PG_CK(cudaSetDevice(g->device));
     cudaStream_t s = (cudaStream_t)stream;
     uint32_t *toff = nullptr, *tidx = nullptr;
-    PG_CK(cudaMalloc(&toff, ((size_t)g->n + 1) * sizeof(uint32_t)));
-    if (cudaMalloc(&tidx, (size_t)(g->m ? g->m : 1) * sizeof(uint32_t)) != cudaSuccess) {
-        cudaFree(toff);
-        return pg_cuda_error(cudaErrorMemoryAllocation, "cudaMalloc(transpose)");
+    PG_CK(dev_alloc(&toff, ((size_t)g->n + 1) * sizeof(uint32_t), s));
+    if (dev_alloc(&tidx, (size_t)(g->m ? g->m : 1) * sizeof(uint32_t), s) != cudaSuccess) {
+        cudaGetLastError();
+        dev_free_idle(toff);
+        return pg_cuda_error(cudaErrorMemoryAllocation, "cudaMallocAsync(transpose)");
     }
     pg_status st = copy_in(toff, t_offsets, (size_t)g->n + 1, s);
     if (!st) st = copy_in(tidx, t_indices, g->m, s);
     if (!st) st = validate(g, toff, tidx, g->n, g->m, s);
-    if (st) { cudaFree(toff); cudaFree(tidx); return st; }
-    if (!g->transpose_is_self) { cudaFree(g->d_toff); cudaFree(g->d_tidx); }
-    if (g->d_ell[1] && g->d_ell[1] != g->d_ell[0]) cudaFree(g->d_ell[1]);
+    if (st) { dev_free_idle(toff); dev_free_idle(tidx); return st; }
+    if (!g->transpose_is_self) { dev_free_idle(g->d_toff); dev_free_idle(g->d_tidx); }
+    if (g->d_ell[1] && g->d_ell[1] != g->d_ell[0]) dev_free_idle(g->d_ell[1]);
     pg_msbfs_release(g);  // its in-edge chunk list refers to the old transpose
     g->d_ell[1] = nullptr;
     g->ellw[1] = 0;
@@ -531,7 +602,10 @@ extern "C" pg_status pg_set_schedule_weights(pg_graph *g, const float *w, size_t
     if (nfloats != PG_MLP_NPARAMS)
         return pg_set_error(PG_ERR_INVALID_ARG, "weights: %zu floats, expected %u", nfloats, PG_MLP_NPARAMS);
     PG_CK(cudaSetDevice(g->device));
-    if (!g->d_weights) PG_CK(cudaMalloc(&g->d_weights, PG_MLP_NPARAMS * sizeof(float)));
+    if (!g->d_weights) {
+        PG_CK(dev_alloc(&g->d_weights, PG_MLP_NPARAMS * sizeof(float), 0));
+        PG_CK(cudaStreamSynchronize(0));
+    }
     const cudaMemcpyKind kind = pg_is_device_ptr(w) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     PG_CK(cudaMemcpy(g->d_weights, w, PG_MLP_NPARAMS * sizeof(float), kind));
     g->has_weights = true;
@@ -595,7 +669,7 @@ extern "C" pg_status pg_bfs(pg_graph *g, uint32_t src, uint32_t *dist_out, const
     PG_CK(cudaSetDevice(g->device));
     cudaStream_t s = (cudaStream_t)stream;
     PgLaunch L;
-    pg_status st = pg_resolve_config(g, cfg, &L);
+    pg_status st = pg_resolve_config(g, cfg, &L, s);
     if (st) return st;
     if (L.ref_dist && !L.trace) L.ref_dist = nullptr;
     L.epoch = g->epoch;
@@ -603,7 +677,7 @@ extern "C" pg_status pg_bfs(pg_graph *g, uint32_t src, uint32_t *dist_out, const
     const bool host_out = !pg_is_device_ptr(dist_out);
     if (host_out) {
         void *p = nullptr;
-        st = pg_stage(g, (size_t)g->n * sizeof(uint32_t), &p);
+        st = pg_stage(g, (size_t)g->n * sizeof(uint32_t), &p, s);
         if (st) return st;
         dev = (uint32_t *)p;
     }
@@ -629,7 +703,7 @@ extern "C" pg_status pg_reach_multi(pg_graph *g, const uint32_t *sources, uint32
     PG_CK(cudaSetDevice(g->device));
     cudaStream_t s = (cudaStream_t)stream;
     PgLaunch L;
-    pg_status st = pg_resolve_config(g, cfg, &L);
+    pg_status st = pg_resolve_config(g, cfg, &L, s);
     if (st) return st;
     L.ref_dist = nullptr;
     L.epoch = g->epoch;
@@ -640,7 +714,7 @@ extern "C" pg_status pg_reach_multi(pg_graph *g, const uint32_t *sources, uint32
     const bool hb = (dir & PG_BWD) && !pg_is_device_ptr(bwd_out);
     if (hf || hb) {
         void *p = nullptr;
-        st = pg_stage(g, bytes * 2, &p);
+        st = pg_stage(g, bytes * 2, &p, s);
         if (st) return st;
         if (hf) f = (unsigned long long *)p;
         if (hb) b = (unsigned long long *)((char *)p + bytes);
@@ -661,14 +735,14 @@ extern "C" pg_status pg_bfs_multi(pg_graph *g, const uint32_t *sources, uint32_t
     PG_CK(cudaSetDevice(g->device));
     cudaStream_t s = (cudaStream_t)stream;
     PgLaunch L;
-    pg_status st = pg_resolve_config(g, cfg, &L);
+    pg_status st = pg_resolve_config(g, cfg, &L, s);
     if (st) return st;
     const size_t bytes = (size_t)k * g->n * sizeof(uint32_t);
     uint32_t *dev = dist_out;
     const bool host_out = !pg_is_device_ptr(dist_out);
     if (host_out) {
         void *p = nullptr;
-        st = pg_stage(g, bytes, &p);
+        st = pg_stage(g, bytes, &p, s);
         if (st) return st;
         dev = (uint32_t *)p;
     }
@@ -703,7 +777,7 @@ extern "C" pg_status pg_count_reached(pg_graph *g, const uint32_t *dist, uint64_
     PG_CK(cudaSetDevice(g->device));
     cudaStream_t s = (cudaStream_t)stream;
     void *p = nullptr;
-    pg_status st = pg_stage(g, 16, &p);
+    pg_status st = pg_stage(g, 16, &p, s);
     if (st) return st;
     PG_CK(cudaMemsetAsync(p, 0, 16, s));
     k_count_reached<<<g->num_sms * 4, 256, 0, s>>>(g->d_off, dist, g->n, (unsigned long long *)p);

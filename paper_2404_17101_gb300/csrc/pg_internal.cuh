@@ -206,8 +206,8 @@ struct PgLaunch {
     uint32_t cta_queue;  // CTA level-buffer capacity
 };
 
-pg_status pg_resolve_config(pg_graph *g, const pg_config *cfg, PgLaunch *L);
-pg_status pg_stage(pg_graph *g, size_t bytes, void **dev);
+pg_status pg_resolve_config(pg_graph *g, const pg_config *cfg, PgLaunch *L, cudaStream_t s);
+pg_status pg_stage(pg_graph *g, size_t bytes, void **dev, cudaStream_t s);
 // out[i] = in[0] + ... + in[i-1] for i < len (device arrays, stream-ordered)
 pg_status pg_exclusive_scan(const uint32_t *in, uint32_t *out, uint32_t len, cudaStream_t s);
 bool pg_is_device_ptr(const void *p);

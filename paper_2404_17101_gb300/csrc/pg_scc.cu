@@ -410,7 +410,7 @@ extern "C" pg_status pg_scc(pg_graph *g, uint32_t *label_out, const pg_config *c
     const bool host_out = !pg_is_device_ptr(label_out);
     if (host_out) {
         void *p = nullptr;
-        pg_status st = pg_stage(g, (size_t)n * sizeof(uint32_t), &p);
+        pg_status st = pg_stage(g, (size_t)n * sizeof(uint32_t), &p, s);
         if (st) return st;
         out = (uint32_t *)p;
     }
