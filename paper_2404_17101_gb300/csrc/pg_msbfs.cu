@@ -21,6 +21,7 @@
 namespace {
 constexpr uint32_t kHeavy = 32;    // edges: below, one thread (bottom-up) / one lane (top-down)
 constexpr uint32_t kChunk = 1024;  // edges per chunk of a heavy vertex
+constexpr uint32_t kGather = 8;    // bottom-up: in-neighbour gathers in flight per light vertex
 }  // namespace
 
 struct PgMsbfsWork {
@@ -163,19 +164,19 @@ __global__ void __launch_bounds__(512) pg_msbfs_kernel(const MsArgs A) {
         edges_seen += E;
         if (bottom_up) {
             pulls++;
-            // light vertices: one thread each, four gathers in flight
+            // light vertices: one thread each, kGather gathers in flight
             for (uint32_t w = gtid; w < n; w += gthreads) {
                 const unsigned long long need = full & ~A.seen[w];
                 if (!need) continue;
                 const uint32_t b = __ldg(A.G.toff + w), e = __ldg(A.G.toff + w + 1);
                 if (e - b >= kHeavy) continue;  // in the chunk list
                 unsigned long long acc = 0;
-                for (uint32_t q = b; q < e; q += 4) {
-                    uint32_t u[4];
+                for (uint32_t q = b; q < e; q += kGather) {
+                    uint32_t u[kGather];
 #pragma unroll
-                    for (int i = 0; i < 4; i++) u[i] = (q + i < e) ? __ldg(A.G.tidx + q + i) : PG_NONE;
+                    for (int i = 0; i < (int)kGather; i++) u[i] = (q + i < e) ? __ldg(A.G.tidx + q + i) : PG_NONE;
 #pragma unroll
-                    for (int i = 0; i < 4; i++)
+                    for (int i = 0; i < (int)kGather; i++)
                         if (u[i] != PG_NONE) acc |= __ldcg(A.visit + u[i]);
                     if ((acc & need) == need) break;
                 }

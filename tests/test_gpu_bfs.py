@@ -216,3 +216,20 @@ def test_upload_from_device_tensors(pg):
     G = pg.Graph.upload(off, idx)
     d, _ = _bfs(pg, G, 17)
     assert np.array_equal(d, oracle.bfs(g, 17))
+
+
+def test_upload_free_cycles_reuse_pool_memory(pg):
+    """Graphs of different sizes uploaded and freed in turn (their buffers
+    are recycled through the device memory pool) keep giving exact results,
+    including host-output calls that stage through a pooled buffer."""
+    graphs = [gg.knn(30_000, 5, 3), gg.dgrid(90, 110, 2, shortcuts=5), gg.knn(8_000, 3, 4)]
+    want = [oracle.bfs(g, 1) for g in graphs]
+    for cycle in range(4):
+        for g, w in zip(graphs, want):
+            G = pg.Graph.from_graphgen(g, ell=(cycle % 2 == 0))
+            d, _ = _bfs(pg, G, 1)
+            assert np.array_equal(d, w), (cycle, g.name)
+            h = np.empty(g.n, dtype=np.uint32)
+            G.bfs_host(1, h)
+            assert np.array_equal(h, w), (cycle, g.name)
+            G.free()
