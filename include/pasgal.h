@@ -53,7 +53,9 @@ typedef enum pg_status {
 
 /* schedules (pg_config.schedule) */
 #define PG_SCHED_FIXED 0u   /* fixed tau; push/pull by the Beamer test if direction = AUTO */
-#define PG_SCHED_LEARNED 1u /* per-round action from the schedule MLP (weights required) */
+#define PG_SCHED_LEARNED 1u /* per-round action from the schedule MLP (weights required), judged
+                               against the fixed push action tau = cfg->tau: the network's choice
+                               is taken only when its predicted gain exceeds a margin */
 #define PG_SCHED_RANDOM 2u  /* uniformly random action per round (trace collection) */
 #define PG_SCHED_SCRIPT 3u  /* per-round action read from cfg->script (tests) */
 
@@ -76,7 +78,11 @@ typedef enum pg_status {
 #define PG_ACTION_PULL 7u
 
 /* Schedule MLP: 5 inputs -> 32 ReLU -> 32 ReLU -> 8 outputs, fp32,
- * packed W1[32][5], b1[32], W2[32][32], b2[32], W3[8][32], b3[8]. */
+ * packed W1[32][5], b1[32], W2[32][32], b2[32], W3[8][32], b3[8].
+ * Inputs of round r (F = frontier entries, E = their out-edges, t = the
+ * previous round's time in microseconds): log2(1+F)/24, log2(1+E)/32,
+ * log2(1+E/F)/8, log2(1+min(r, 2^14))/24, log2(1+t)/16.  Outputs: one score
+ * per action (higher = faster predicted). */
 #define PG_MLP_IN 5u
 #define PG_MLP_HID 32u
 #define PG_MLP_NPARAMS 1512u
