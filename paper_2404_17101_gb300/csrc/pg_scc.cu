@@ -308,9 +308,16 @@ __global__ void k_scc_assign(uint32_t n, uint32_t *part, const unsigned long lon
     if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(active, cnt);
 }
 
+// mn[rep] = smallest vertex of each SCC.  Threads visit vertices in rising
+// id order, so a component's minimum is found early and almost every later
+// member sees a smaller value and skips the atomic: one giant component
+// would otherwise serialise millions of same-address atomics.
 __global__ void k_scc_min(uint32_t n, const uint32_t *rep, uint32_t *mn) {
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) atomicMin(mn + rep[v], v);
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const uint32_t r = rep[v];
+        if (__ldcg(mn + r) > v) atomicMin(mn + r, v);
+    }
 }
 
 __global__ void k_scc_label(uint32_t n, const uint32_t *rep, const uint32_t *mn, uint32_t *out) {
