@@ -4,13 +4,16 @@
                                            [--learned] [--out dist.u32]
     python -m paper_2404_17101_gb300 reach --input g.adj --sources 0,5,9 [--directed] [--out masks.u64]
     python -m paper_2404_17101_gb300 scc   --input g.adj [--directed] [--out labels.u32]
+    python -m paper_2404_17101_gb300 bfs64 --input g.adj [--sources ...] [--out dist.u32]
 
 `--input` reads the PBBS "AdjacencyGraph" text format; `--workload` takes a
 named generator of the graphgen module instead (e.g. knn_10m, grid_1000).
 One JSON line with the device time (kernel events), rounds and, for BFS, the
 traversed edges and GTEPS is printed; `--out` writes the result as raw
 little-endian integers (uint32 distances / labels, uint64 masks: forward, then
-backward).  Needs a CUDA GPU; there is no CPU fallback.
+backward; bfs64: 64 x n distances, source-major).  Without --sources, reach
+and bfs64 take 64 seeded sources of out-degree > 0.  Needs a CUDA GPU; there
+is no CPU fallback.
 """
 from __future__ import annotations
 
@@ -29,13 +32,13 @@ if ROOT not in sys.path:
 def _args(argv):
     ap = argparse.ArgumentParser(prog="python -m paper_2404_17101_gb300",
                                  description="Exact BFS, reachability and SCC on one GB300.")
-    ap.add_argument("op", choices=["bfs", "reach", "scc"])
+    ap.add_argument("op", choices=["bfs", "reach", "scc", "bfs64"])
     src = ap.add_mutually_exclusive_group(required=True)
     src.add_argument("--input", help="graph in the PBBS AdjacencyGraph text format")
     src.add_argument("--workload", help="named graphgen generator, e.g. knn_10m, grid_1000, dgrid_4000")
     ap.add_argument("--directed", action="store_true", help="arcs as given (else the file is symmetric)")
     ap.add_argument("--source", type=int, default=0, help="bfs: source vertex")
-    ap.add_argument("--sources", default="0", help="reach: comma-separated sources (at most 64)")
+    ap.add_argument("--sources", default="", help="reach / bfs64: comma-separated sources (at most 64)")
     ap.add_argument("--backward", action="store_true", help="reach: also the backward masks")
     ap.add_argument("--tau", type=int, default=0, help="VGC hop window (0 = library default)")
     ap.add_argument("--learned", action="store_true", help="bfs: learned per-round schedule")
@@ -72,13 +75,20 @@ def main(argv=None) -> int:
         rec.update(source=a.source, reached=n_r, traversed_edges=m_r,
                    gteps=m_r / st.kernel_ms / 1e6 if st.kernel_ms else None)
         out = pg.to_uint32(d)
-    elif a.op == "reach":
+    elif a.op in ("reach", "bfs64"):
         srcs = np.array([int(x) for x in a.sources.split(",") if x], dtype=np.uint32)
+        if len(srcs) == 0:
+            srcs = gg.pick_sources(g, min(64, g.n), 3)
+    if a.op == "bfs64":
+        D = G.bfs_multi(srcs, cfg=pg.default_config(direction=pg.PG_DIR_AUTO, **kw), stats=st)
+        out = pg.to_uint32(D).reshape(-1)
+        rec.update(sources=len(srcs), pull_rounds=st.pull_rounds)
+    elif a.op == "reach":
         direction = pg.PG_FWD | (pg.PG_BWD if a.backward else 0)
         f, b = G.reach_multi(srcs, direction, cfg=pg.default_config(**kw), stats=st)
         out = pg.to_uint64(f) if b is None else np.concatenate([pg.to_uint64(f), pg.to_uint64(b)])
         rec.update(sources=len(srcs))
-    else:
+    elif a.op == "scc":
         lab, it = G.scc(cfg=pg.default_config(**kw), stats=st)
         out = pg.to_uint32(lab)
         rec.update(components=int(len(np.unique(out))), iterations=it)

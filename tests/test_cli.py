@@ -52,3 +52,8 @@ def test_bfs_reach_scc_on_a_file(tmp_path):
     r = _run(["scc", "--input", p, "--directed", "--out", out])
     assert r.returncode == 0, r.stderr
     assert np.array_equal(np.fromfile(out, dtype="<u4"), oracle.scc(g))
+    out = str(tmp_path / "D.u32")
+    r = _run(["bfs64", "--input", p, "--directed", "--sources", "3,77,1000", "--out", out])
+    assert r.returncode == 0, r.stderr
+    D = np.fromfile(out, dtype="<u4").reshape(3, g.n)
+    assert np.array_equal(D, oracle.bfs_multi(g, np.array([3, 77, 1000], dtype=np.uint32)))
