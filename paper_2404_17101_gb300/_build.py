@@ -46,7 +46,9 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     lib = out or LIB
     if not force and out is None and up_to_date():
         return LIB
-    build_dir = BUILD + tag
+    # objects go to a per-process directory, so that processes building at the
+    # same time (e.g. one per rank) never write the same object file
+    build_dir = f"{BUILD}{tag}.{os.getpid()}"
     os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
     flags = NVCC_FLAGS + (extra or [])
@@ -69,6 +71,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, lib)
+    shutil.rmtree(build_dir, ignore_errors=True)
     return lib
 
 
