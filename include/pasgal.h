@@ -281,11 +281,17 @@ pg_status pg_autotune(pg_graph *g, uint32_t kind, const uint32_t *sources, uint3
  *  cfg: NULL or a fixed push schedule (tau, chunk, launch shape, timeout);
  *    learned/scripted schedules, pull rounds and traces -> PG_ERR_UNSUPPORTED.
  *    High-degree vertices are not split across warps here.
+ *  The three buffers must be memory of the CURRENT device (another device's
+ *    memory -> PG_ERR_INVALID_ARG); the call runs there.
  *  Scratch lives in a fixed array of PG_NOALLOC_SCRATCH_BYTES compiled into
  *    the library (held by every GPU that loads it until exit) and shared by
  *    all calls on a device: calls that overlap on the GPU race, so serialise
  *    them per device.  The first call on a device looks up the array's
  *    address (cudaGetSymbolAddress); make it before any stream capture.
+ *  The call is synchronous (it waits on `stream` for the CSR check and for
+ *    its status word, copying both into host memory), so it cannot be
+ *    recorded into a CUDA graph.  Calls on different devices do not wait
+ *    for each other.
  *  No cudaMalloc, cudaFree or allocating library routine is called.
  */
 #define PG_NOALLOC_MAX_N (1u << 20)

@@ -333,11 +333,31 @@ def bfs_noalloc(offsets, indices, src: int, out, cfg: Config | None = None, stre
 
     For callers that cannot allocate device memory at call time: the library
     uses a fixed scratch array instead of allocating.  offsets/indices/out
-    must already live on the device; n <= NOALLOC_MAX_N."""
+    must be contiguous int32 or uint32 tensors on one CUDA device, with
+    out.numel() >= n = offsets.numel() - 1 and n <= NOALLOC_MAX_N.  The C ABI
+    cannot see buffer sizes, so they are checked here (ValueError) before
+    anything is launched; the call runs on the tensors' device."""
+    import torch
+    for name, t in (("offsets", offsets), ("indices", indices), ("out", out)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"bfs_noalloc: {name} must be a torch tensor")
+        if t.dtype not in (torch.int32, torch.uint32):
+            raise ValueError(f"bfs_noalloc: {name} must be int32 or uint32, not {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"bfs_noalloc: {name} must be contiguous")
     n = offsets.numel() - 1
-    _check(load().pg_bfs_noalloc(ctypes.c_void_p(offsets.data_ptr()), ctypes.c_void_p(indices.data_ptr()),
-                                 n, indices.numel(), int(src), ctypes.c_void_p(out.data_ptr()),
-                                 ctypes.byref(cfg) if cfg else None, _stream_ptr(stream)))
+    if n < 1:
+        raise ValueError("bfs_noalloc: offsets must hold n + 1 >= 2 entries")
+    if out.numel() < n:
+        raise ValueError(f"bfs_noalloc: out holds {out.numel()} entries, fewer than n = {n}")
+    devs = {t.device for t in (offsets, indices, out)}
+    if len(devs) != 1 or next(iter(devs)).type != "cuda":
+        raise ValueError(f"bfs_noalloc: offsets, indices and out must be on one CUDA device, got {devs}")
+    with torch.cuda.device(out.device):
+        _check(load().pg_bfs_noalloc(ctypes.c_void_p(offsets.data_ptr()),
+                                     ctypes.c_void_p(indices.data_ptr()), n, indices.numel(),
+                                     int(src), ctypes.c_void_p(out.data_ptr()),
+                                     ctypes.byref(cfg) if cfg else None, _stream_ptr(stream)))
     return out
 
 

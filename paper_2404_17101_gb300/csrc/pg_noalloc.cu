@@ -23,6 +23,13 @@
 // call on each device looks the address up with cudaGetSymbolAddress while
 // that device is current and keeps it; that first call therefore performs a
 // runtime lookup and should be made before any stream capture begins.
+//
+// Every call is synchronous: it waits on its stream twice (for the CSR
+// check and for the status word) and copies both results into host stack
+// memory, so no call can be recorded into a CUDA graph.  The caller's three
+// buffers must live on the current device (the one whose scratch array is
+// used); a buffer on another device is rejected.  Calls on different
+// devices take different locks and do not wait for each other.
 #include <mutex>
 
 #include "pg_internal.cuh"
@@ -43,14 +50,26 @@ static_assert(kScratchBytes <= PG_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds
 static __device__ __align__(256) unsigned char g_bfs_scratch[PG_NOALLOC_SCRATCH_BYTES];
 
 struct DeviceScratch {
+    std::mutex mu;                  // serialises the host side of calls on this device
     bool ready = false;
     unsigned char *base = nullptr;  // device address of g_bfs_scratch on this device
     uint32_t epoch = 1;             // round-tag base for the next call
 };
 
 constexpr int kMaxDevices = 64;
-std::mutex g_mu;
 DeviceScratch g_dev[kMaxDevices];
+
+// True when p is device (or managed) memory that belongs to device `dev`.
+bool on_device(const void *p, int dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeDevice) return a.device == dev;
+    // managed memory is reachable from every device of the process
+    return a.type == cudaMemoryTypeManaged;
+}
 
 // CSR checks (same rules as pg_graph_upload); bit flags into *bad.
 __global__ void k_noalloc_validate(const uint32_t *off, const uint32_t *idx, uint32_t n, uint32_t m,
@@ -79,8 +98,13 @@ extern "C" pg_status pg_bfs_noalloc(const uint32_t *offsets, const uint32_t *ind
                             "vertices; use pg_graph_upload + pg_bfs for larger graphs)",
                             n, PG_NOALLOC_MAX_N, PG_NOALLOC_MAX_N);
     if (src >= n) return pg_set_error(PG_ERR_INVALID_ARG, "src %u >= n %u", src, n);
-    if (!pg_is_device_ptr(offsets) || (m && !pg_is_device_ptr(indices)) || !pg_is_device_ptr(dist_out))
-        return pg_set_error(PG_ERR_INVALID_ARG, "pg_bfs_noalloc: offsets, indices and dist_out must be device memory");
+    int dev = 0;
+    PG_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return pg_set_error(PG_ERR_UNSUPPORTED, "device %d", dev);
+    if (!on_device(offsets, dev) || (m && !on_device(indices, dev)) || !on_device(dist_out, dev))
+        return pg_set_error(PG_ERR_INVALID_ARG,
+                            "pg_bfs_noalloc: offsets, indices and dist_out must be device memory "
+                            "of the current device (%d)", dev);
     pg_config d;
     pg_config_default(&d);
     const pg_config *c = cfg ? cfg : &d;
@@ -118,12 +142,9 @@ extern "C" pg_status pg_bfs_noalloc(const uint32_t *offsets, const uint32_t *ind
     L.stall_block = c->test_stall_block;
     L.allow_pull = 0;
 
-    int dev = 0;
-    PG_CK(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return pg_set_error(PG_ERR_UNSUPPORTED, "device %d", dev);
     cudaStream_t s = (cudaStream_t)stream;
-    std::lock_guard<std::mutex> lock(g_mu);
     DeviceScratch &D = g_dev[dev];
+    std::lock_guard<std::mutex> lock(D.mu);
     if (!D.ready) {
         // one-time set-up on this device (it is current): the array's device address
         void *p = nullptr;

@@ -66,3 +66,21 @@ def test_no_cpu_fallback_without_library(monkeypatch):
     monkeypatch.setattr(pg, "_lib", None)
     with pytest.raises(RuntimeError):
         pg.load("/nonexistent/libpasgal_gb.so")
+
+
+def test_bfs_noalloc_wrapper_rejects_bad_buffers_before_any_launch():
+    """The C ABI cannot see buffer sizes, so the binding checks dtype,
+    contiguity, sizes and device before calling pg_bfs_noalloc; each failure
+    is a ValueError raised before the library is even loaded (CPU tensors)."""
+    import torch
+    import paper_2404_17101_gb300 as pg
+    off = torch.tensor([0, 1, 2], dtype=torch.int32)
+    idx = torch.tensor([1, 0], dtype=torch.int32)
+    with pytest.raises(ValueError, match="fewer than n"):
+        pg.bfs_noalloc(off, idx, 0, torch.empty(1, dtype=torch.int32))
+    with pytest.raises(ValueError, match="int32 or uint32"):
+        pg.bfs_noalloc(off, idx, 0, torch.empty(2, dtype=torch.int64))
+    with pytest.raises(ValueError, match="contiguous"):
+        pg.bfs_noalloc(off, idx, 0, torch.empty(4, dtype=torch.int32)[::2])
+    with pytest.raises(ValueError, match="CUDA device"):
+        pg.bfs_noalloc(off, idx, 0, torch.empty(2, dtype=torch.int32))

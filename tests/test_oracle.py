@@ -236,3 +236,17 @@ def test_reached_edges_counts():
     d = oracle.bfs(g, 0)
     reached = d != INF
     assert oracle.reached_edges(g, d) == (int(reached.sum()), int(g.degrees()[reached].sum()))
+
+
+def test_parallel_oracle_helper_matches_serial_oracle():
+    """The test helper that splits multi-source oracle questions into chunks
+    run on several cores returns exactly what one serial call returns."""
+    import _oracle_par as par
+    g = gg.dgrid(40, 50, 9)
+    srcs = gg.pick_sources(g, 20, 3)
+    for back in (False, True):
+        assert np.array_equal(par.reach(g, srcs, backward=back, chunk=8),
+                              oracle.reach(g, srcs, backward=back))
+    rows = par.bfs_rows(g, srcs[:5])
+    for s in srcs[:5]:
+        assert np.array_equal(rows[int(s)], oracle.bfs(g, int(s)))

@@ -90,6 +90,35 @@ def test_adam_closed_form_first_steps():
     assert np.allclose(p2, p1 - lr * g / (np.abs(g) + eps), rtol=1e-12, atol=1e-15)
 
 
+def test_adam_moment_decay_under_varying_gradients():
+    """Adam's moment decay rates (Kingma & Ba 2015, Algorithm 1) pinned by
+    hand-derived values.  A constant gradient hides beta1 and beta2 (the
+    bias-corrected moments equal g and g^2 for any betas), so this uses
+    g = 1, 3, -2 with beta1 = 0.5 and beta2 = 0.75.  Unrolling the moment
+    recursions gives the bias-corrected moments as weighted means:
+      m_hat_t = sum_i beta1^(t-i) g_i / sum_i beta1^(t-i)
+      v_hat_t = sum_i beta2^(t-i) g_i^2 / sum_i beta2^(t-i)
+    which for these numbers are, by hand:
+      t = 1: m_hat = 1,     v_hat = 1
+      t = 2: m_hat = 7/3,   v_hat = 39/7
+      t = 3: m_hat = -1/7,  v_hat = 181/37
+    and raw moments after step 3: m = 0.5 * (-0.25) = -0.125,
+    v = 0.25 * (181/16) = 2.828125.  Swapping the betas gives
+    m_hat_2 = 15/7 instead of 7/3, so a swap fails this test."""
+    p0 = np.array([0.3])
+    m = np.zeros(1)
+    v = np.zeros(1)
+    lr = 0.1
+    steps = [(1.0, 1.0, 1.0), (3.0, 7.0 / 3.0, 39.0 / 7.0), (-2.0, -1.0 / 7.0, 181.0 / 37.0)]
+    p = p0
+    for t, (g, mh, vh) in enumerate(steps, start=1):
+        p_next, m, v = mlp.adam_step(p, np.array([g]), m, v, t, lr=lr, beta1=0.5, beta2=0.75,
+                                     eps=0.0)
+        assert np.allclose(p_next, p - lr * mh / np.sqrt(vh), rtol=1e-13, atol=0), t
+        p = p_next
+    assert np.isclose(m[0], -0.125, rtol=1e-13) and np.isclose(v[0], 2.828125, rtol=1e-13)
+
+
 def test_features_closed_form():
     X = mlp.features([1, 0, 3], [3, 0, 21], [0, 1, 3], [1000, 0, 3000])
     assert np.allclose(X[0], [1 / 24, 2 / 32, 2 ** 0 * np.log2(4) / 8, 0, 1 / 16])

@@ -1,17 +1,20 @@
-"""The allocation-free BFS entry point (pg_bfs_noalloc) against pg_bfs.
+"""The allocation-free BFS entry point (pg_bfs_noalloc) against the oracle
+and against pg_bfs.
 
 pg_bfs_noalloc serves callers that cannot allocate device memory at call
 time (a framework memory pool that owns the device, a loop where
 cudaMalloc's implicit synchronisation is not allowed): it works on the
 caller's device CSR and output and keeps its scratch in a fixed array
-compiled into the library.  Its distances must equal pg_bfs's bit for bit
-(hop distances are integers), on two calls in a row, since every call
-reuses the same scratch.  This file is collected last on purpose.
+compiled into the library.  Its distances must equal the oracle's and
+pg_bfs's bit for bit (hop distances are integers), on two calls in a row,
+since every call reuses the same scratch; one case fills the scratch to its
+stated maximum (n = 2^20 vertices).  This file is collected last on purpose.
 """
 import numpy as np
 import pytest
 
 import graphgen as gg
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -36,9 +39,30 @@ def test_noalloc_matches_pg_bfs_on_consecutive_calls(pg, make, srcs):
         s = int(s) % g.n
         out = torch.full((g.n,), -7, dtype=torch.int32, device="cuda")
         pg.bfs_noalloc(off, idx, s, out, cfg=pg.default_config(tau=8))
+        got = pg.to_uint32(out)
+        assert np.array_equal(got, oracle.bfs(g, s)), (g.name, s)
         want = pg.to_uint32(G.bfs(s, cfg=pg.default_config(tau=8)))
-        assert np.array_equal(pg.to_uint32(out), want), (g.name, s)
+        assert np.array_equal(got, want), (g.name, s)
     torch.cuda.synchronize()
+
+
+def test_noalloc_at_the_maximum_size(pg):
+    """n = PG_NOALLOC_MAX_N (a 1024 x 1024 grid) uses the whole bag and round-
+    tag extent of the fixed scratch; two calls in a row, closed form
+    dist(r, c) = |r - r0| + |c - c0| and the oracle."""
+    import torch
+    g = gg.grid(1024, 1024)
+    assert g.n == pg.NOALLOC_MAX_N
+    off, idx = _dev(g.offsets), _dev(g.indices)
+    r, c = np.meshgrid(np.arange(1024), np.arange(1024), indexing="ij")
+    for s in (0, 1024 * 700 + 300):
+        out = torch.full((g.n,), -7, dtype=torch.int32, device="cuda")
+        pg.bfs_noalloc(off, idx, s, out)
+        got = pg.to_uint32(out)
+        r0, c0 = divmod(s, 1024)
+        want = (np.abs(r - r0) + np.abs(c - c0)).astype(np.uint32).reshape(-1)
+        assert np.array_equal(got, want), s
+        assert np.array_equal(got, oracle.bfs(g, s)), s
 
 
 def test_noalloc_rejects_what_it_cannot_hold(pg):
