@@ -62,10 +62,15 @@ def _load():
         lib.gg_free.argtypes = [P(_CSR)]
         lib.gg_read_adj.argtypes = [ctypes.c_char_p, P(_CSR)]
         lib.gg_write_adj.argtypes = [ctypes.c_char_p, u32, u32, ctypes.c_void_p, ctypes.c_void_p]
+        lib.gg_read_gbbs_bin.argtypes = [ctypes.c_char_p, P(_CSR)]
+        lib.gg_edge_weights.argtypes = [u32, ctypes.c_void_p, ctypes.c_void_p, u32, u32, u64,
+                                        ctypes.c_void_p]
+        lib.gg_write_gbbs_bin.argtypes = [ctypes.c_char_p, u32, u32, ctypes.c_void_p, ctypes.c_void_p]
         lib.gg_rand.argtypes = [u64, u64, u64]
         lib.gg_rand.restype = u64
         for f in ("gg_grid", "gg_dgrid", "gg_knn", "gg_rmat", "gg_random", "gg_from_arcs",
-                  "gg_pick_sources", "gg_num_threads", "gg_read_adj", "gg_write_adj"):
+                  "gg_pick_sources", "gg_num_threads", "gg_read_adj", "gg_write_adj",
+                  "gg_read_gbbs_bin", "gg_write_gbbs_bin", "gg_edge_weights"):
             getattr(lib, f).restype = i32
         _lib = lib
     return _lib
@@ -182,6 +187,35 @@ def write_adj(g: Graph, path: str) -> None:
     idx = np.ascontiguousarray(g.indices, dtype=np.uint32)
     _check(_load().gg_write_adj(os.fsencode(path), g.n, g.m, off.ctypes.data, idx.ctypes.data),
            f"write_adj({path})")
+
+
+def edge_weights(g: Graph, lo: int, hi: int, seed: int) -> np.ndarray:
+    """Seeded uint32 weights in [lo, hi] (lo >= 1), one per arc of g, drawn per
+    unordered vertex pair so that both arcs of an undirected edge agree."""
+    out = np.empty(max(g.m, 1), dtype=np.uint32)
+    off = np.ascontiguousarray(g.offsets, dtype=np.uint32)
+    idx = np.ascontiguousarray(g.indices, dtype=np.uint32)
+    _check(_load().gg_edge_weights(g.n, off.ctypes.data, idx.ctypes.data, lo, hi, seed,
+                                   out.ctypes.data), "edge_weights")
+    return out[:g.m]
+
+
+def read_gbbs_bin(path: str, directed: bool = True) -> Graph:
+    """Read a graph in the GBBS binary layout: 64-bit header words n, m and
+    the file size, n + 1 64-bit offsets, m 32-bit targets (little-endian).
+    Arcs are taken as given; `directed=False` marks a file that stores both
+    directions of every edge."""
+    c = _CSR()
+    _check(_load().gg_read_gbbs_bin(os.fsencode(path), ctypes.byref(c)), f"read_gbbs_bin({path})")
+    return _take(c, directed, os.path.basename(path), path=path)
+
+
+def write_gbbs_bin(g: Graph, path: str) -> None:
+    """Write g in the GBBS binary layout (see read_gbbs_bin)."""
+    off = np.ascontiguousarray(g.offsets, dtype=np.uint32)
+    idx = np.ascontiguousarray(g.indices, dtype=np.uint32)
+    _check(_load().gg_write_gbbs_bin(os.fsencode(path), g.n, g.m, off.ctypes.data, idx.ctypes.data),
+           f"write_gbbs_bin({path})")
 
 
 def pick_sources(g: Graph, k: int, seed: int) -> np.ndarray:

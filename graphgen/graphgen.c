@@ -550,3 +550,79 @@ int gg_write_adj(const char *path, uint32_t n, uint32_t m, const uint32_t *offse
     if (fclose(f) != 0) ok = 0;
     return ok ? GG_OK : GG_ERR_IO;
 }
+
+/* The GBBS binary graph layout (the binary format the paper's experiments
+ * read, Sec. 4 Setup; the paper names it but does not print it).  Read here
+ * as: three little-endian 64-bit header words n, m and the file's size in
+ * bytes, then n + 1 64-bit offsets, then m 32-bit targets.  The file must
+ * hold exactly 24 + 8(n+1) + 4m bytes; the third header word is checked
+ * against that size.  Offsets must start at 0, not decrease and end at m;
+ * targets must be < n.  n < 2^31 and m < 2^32 (this library's ids). */
+static int read_exact(FILE *f, void *p, size_t bytes) { return fread(p, 1, bytes, f) == bytes ? 0 : -1; }
+
+int gg_read_gbbs_bin(const char *path, gg_csr *out) {
+    if (!path || !out) return GG_ERR_ARG;
+    memset(out, 0, sizeof(*out));
+    FILE *f = fopen(path, "rb");
+    if (!f) return GG_ERR_IO;
+    uint64_t h[3];
+    if (read_exact(f, h, sizeof(h))) { fclose(f); return GG_ERR_FORMAT; }
+    const uint64_t n = h[0], m = h[1];
+    if (n == 0 || n >= 0x80000000ull || m > 0xFFFFFFFFull) { fclose(f); return GG_ERR_FORMAT; }
+    const uint64_t want = 24u + 8u * (n + 1u) + 4u * m;
+    if (h[2] != want || fseek(f, 0, SEEK_END) != 0) { fclose(f); return GG_ERR_FORMAT; }
+    const long size = ftell(f);
+    if (size < 0 || (uint64_t)size != want || fseek(f, 24, SEEK_SET) != 0) { fclose(f); return GG_ERR_FORMAT; }
+    uint64_t *o64 = (uint64_t *)malloc(((size_t)n + 1) * sizeof(uint64_t));
+    uint32_t *off = (uint32_t *)malloc(((size_t)n + 1) * sizeof(uint32_t));
+    uint32_t *idx = (uint32_t *)malloc((size_t)(m ? m : 1) * sizeof(uint32_t));
+    if (!o64 || !off || !idx) { free(o64); free(off); free(idx); fclose(f); return GG_ERR_OOM; }
+    int bad = read_exact(f, o64, ((size_t)n + 1) * sizeof(uint64_t)) ||
+              (m && read_exact(f, idx, (size_t)m * sizeof(uint32_t)));
+    fclose(f);
+    if (!bad && (o64[0] != 0 || o64[n] != m)) bad = 1;
+    for (uint64_t v = 0; v < n && !bad; v++)
+        if (o64[v + 1] < o64[v]) bad = 1;
+    for (uint64_t v = 0; v <= n && !bad; v++) off[v] = (uint32_t)o64[v];
+    for (uint64_t e = 0; e < m && !bad; e++)
+        if (idx[e] >= n) bad = 1;
+    free(o64);
+    if (bad) { free(off); free(idx); return GG_ERR_FORMAT; }
+    out->n = (uint32_t)n; out->m = (uint32_t)m; out->offsets = off; out->indices = idx;
+    return GG_OK;
+}
+
+int gg_write_gbbs_bin(const char *path, uint32_t n, uint32_t m, const uint32_t *offsets,
+                      const uint32_t *indices) {
+    if (!path || !offsets || (m && !indices) || n == 0) return GG_ERR_ARG;
+    FILE *f = fopen(path, "wb");
+    if (!f) return GG_ERR_IO;
+    const uint64_t h[3] = {n, m, 24u + 8u * ((uint64_t)n + 1u) + 4u * (uint64_t)m};
+    int ok = fwrite(h, sizeof(uint64_t), 3, f) == 3;
+    for (uint32_t v = 0; v <= n && ok; v++) {
+        const uint64_t o = offsets[v];
+        ok = fwrite(&o, sizeof(o), 1, f) == 1;
+    }
+    if (ok && m) ok = fwrite(indices, sizeof(uint32_t), m, f) == m;
+    if (fclose(f) != 0) ok = 0;
+    return ok ? GG_OK : GG_ERR_IO;
+}
+
+/* ------------------------------------------------------------ edge weights -- */
+/* Seeded positive weights in [lo, hi] for every arc of a CSR, drawn per
+ * unordered vertex pair {u, w}: the two arcs of an undirected edge (stored
+ * both ways) get the same weight.  out[e] is the weight of arc e. */
+int gg_edge_weights(uint32_t n, const uint32_t *offsets, const uint32_t *indices, uint32_t lo,
+                    uint32_t hi, uint64_t seed, uint32_t *out) {
+    if (!offsets || !out || lo == 0 || hi < lo) return GG_ERR_ARG;
+    const uint64_t span = (uint64_t)hi - lo + 1u;
+#pragma omp parallel for schedule(static)
+    for (int64_t v = 0; v < (int64_t)n; v++) {
+        for (uint32_t e = offsets[v]; e < offsets[v + 1]; e++) {
+            const uint32_t w = indices[e];
+            const uint64_t a = (uint64_t)v < w ? (uint64_t)v : w, b = (uint64_t)v < w ? w : (uint64_t)v;
+            out[e] = lo + (uint32_t)(gg_draw(seed, 0x77u, (a << 32) | b) % span);
+        }
+    }
+    return GG_OK;
+}

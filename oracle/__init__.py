@@ -21,6 +21,11 @@ Contents:
   * ``scc``            strongly connected components by Tarjan's algorithm
                        (the paper's sequential SCC baseline, Sec. 4 Setup),
                        labelled by the smallest vertex id of each component.
+  * ``sssp``           single-source shortest paths with non-negative
+                       uint32 arc weights (Sec. 2.2, the SSSP paragraph) by
+                       Dijkstra's algorithm; uint64 distances,
+                       0xFFFFFFFFFFFFFFFF if unreachable.
+  * ``floyd_warshall_w`` brute-force all-pairs weighted distances (n <= 64).
   * ``mlp``            fp64 forward / backward / Adam of the schedule MLP.
 
 Parity status: every function here is pinned by closed forms, brute force
@@ -38,6 +43,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
 _SRC = os.path.join(_HERE, "oracle.c")
 INF = 0xFFFFFFFF
+INF64 = 0xFFFFFFFFFFFFFFFF
 
 
 def build(force: bool = False) -> str:
@@ -68,6 +74,8 @@ def _load():
         lib.oracle_warshall.argtypes = [u32, vp, vp, vp]
         lib.oracle_reached_edges.argtypes = [u32, vp, vp, vp, vp]
         lib.oracle_scc.argtypes = [u32, vp, vp, vp]
+        lib.oracle_sssp.argtypes = [u32, vp, vp, vp, u32, vp]
+        lib.oracle_floyd_warshall_w.argtypes = [u32, vp, vp, vp, vp]
         lib.oracle_reached_edges.restype = None
         _lib = lib
     return _lib
@@ -150,3 +158,27 @@ def scc(g) -> np.ndarray:
     if rc:
         raise RuntimeError(f"oracle_scc failed ({rc})")
     return lab
+
+
+def sssp(g, weights, src: int) -> np.ndarray:
+    """Shortest-path distances (uint64) from src with arc weights `weights`
+    (uint32, one per arc of g)."""
+    off, idx, w = _u32(g.offsets), _u32(g.indices), _u32(weights)
+    if len(w) != g.m:
+        raise ValueError("one weight per arc")
+    dist = np.empty(g.n, dtype=np.uint64)
+    rc = _load().oracle_sssp(g.n, off.ctypes.data, idx.ctypes.data, w.ctypes.data, int(src),
+                             dist.ctypes.data)
+    if rc:
+        raise ValueError(f"oracle_sssp rc={rc}")
+    return dist
+
+
+def floyd_warshall_w(g, weights) -> np.ndarray:
+    off, idx, w = _u32(g.offsets), _u32(g.indices), _u32(weights)
+    D = np.empty((g.n, g.n), dtype=np.uint64)
+    rc = _load().oracle_floyd_warshall_w(g.n, off.ctypes.data, idx.ctypes.data, w.ctypes.data,
+                                         D.ctypes.data)
+    if rc:
+        raise ValueError(f"oracle_floyd_warshall_w rc={rc}")
+    return D

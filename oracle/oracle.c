@@ -18,6 +18,12 @@
  *    distances and transitive closure for tiny graphs; they pin the queue
  *    BFS itself (an independent definition of the same quantities).
  *  - oracle_transpose: reversed CSR, written here independently.
+ *  - oracle_sssp: single-source shortest paths with non-negative integer
+ *    arc weights (Sec. 2.2, the SSSP paragraph: the output is each vertex's
+ *    shortest-path distance from the source), by Dijkstra's algorithm with
+ *    a binary heap; 64-bit distances, 0xFFFFFFFFFFFFFFFF if unreachable.
+ *  - oracle_floyd_warshall_w: brute-force all-pairs weighted distances for
+ *    tiny graphs; it pins oracle_sssp by an independent definition.
  *  - oracle_scc: strongly connected components (Sec. 2: a maximal vertex
  *    set in which every vertex reaches every other) by Tarjan's algorithm,
  *    the paper's sequential SCC baseline (Sec. 4, Setup); each vertex is
@@ -218,5 +224,93 @@ int oracle_scc(uint32_t n, const uint32_t *offsets, const uint32_t *indices, uin
         }
     }
     free(index); free(low); free(on); free(comp); free(fv); free(fe);
+    return 0;
+}
+
+/* ---------------------------------------------------------------- SSSP -- */
+#define OR_INF64 0xFFFFFFFFFFFFFFFFull
+
+typedef struct { uint64_t d; uint32_t v; } or_item;
+
+static int item_less(or_item a, or_item b) { return a.d < b.d || (a.d == b.d && a.v < b.v); }
+
+static void heap_push(or_item *h, size_t *size, or_item x) {
+    size_t i = (*size)++;
+    while (i > 0) {
+        size_t p = (i - 1) / 2;
+        if (!item_less(x, h[p])) break;
+        h[i] = h[p];
+        i = p;
+    }
+    h[i] = x;
+}
+
+static or_item heap_pop(or_item *h, size_t *size) {
+    or_item top = h[0];
+    or_item last = h[--(*size)];
+    size_t i = 0;
+    for (;;) {
+        size_t c = 2 * i + 1;
+        if (c >= *size) break;
+        if (c + 1 < *size && item_less(h[c + 1], h[c])) c++;
+        if (!item_less(h[c], last)) break;
+        h[i] = h[c];
+        i = c;
+    }
+    if (*size > 0) h[i] = last;
+    return top;
+}
+
+/* Dijkstra: pop the closest unsettled vertex, relax its out-arcs.  Entries
+ * whose distance is stale (a shorter one was pushed later) are skipped. */
+int oracle_sssp(uint32_t n, const uint32_t *offsets, const uint32_t *indices, const uint32_t *weights,
+                uint32_t src, uint64_t *dist) {
+    if (n == 0 || src >= n || !offsets || !dist || (offsets[n] && (!indices || !weights))) return -1;
+    const size_t cap = (size_t)offsets[n] + 1;
+    or_item *heap = (or_item *)malloc(cap * sizeof(or_item));
+    if (!heap) return -2;
+    for (uint32_t v = 0; v < n; v++) dist[v] = OR_INF64;
+    size_t size = 0;
+    dist[src] = 0;
+    or_item s0 = {0, src};
+    heap_push(heap, &size, s0);
+    while (size > 0) {
+        or_item it = heap_pop(heap, &size);
+        if (it.d != dist[it.v]) continue; /* stale */
+        for (uint32_t e = offsets[it.v]; e < offsets[it.v + 1]; e++) {
+            const uint32_t x = indices[e];
+            const uint64_t nd = it.d + weights[e];
+            if (nd < dist[x]) {
+                dist[x] = nd;
+                or_item y = {nd, x};
+                heap_push(heap, &size, y); /* at most one push per arc */
+            }
+        }
+    }
+    free(heap);
+    return 0;
+}
+
+/* All-pairs weighted distances, D[i*n + j], by Floyd-Warshall (n <= 64). */
+int oracle_floyd_warshall_w(uint32_t n, const uint32_t *offsets, const uint32_t *indices,
+                            const uint32_t *weights, uint64_t *D) {
+    if (n == 0 || n > 64 || !offsets || !D) return -1;
+    for (uint32_t i = 0; i < n; i++)
+        for (uint32_t j = 0; j < n; j++) D[(size_t)i * n + j] = (i == j) ? 0 : OR_INF64;
+    for (uint32_t u = 0; u < n; u++)
+        for (uint32_t e = offsets[u]; e < offsets[u + 1]; e++) {
+            uint64_t *d = &D[(size_t)u * n + indices[e]];
+            if (weights[e] < *d) *d = weights[e];
+        }
+    for (uint32_t k = 0; k < n; k++)
+        for (uint32_t i = 0; i < n; i++) {
+            const uint64_t dik = D[(size_t)i * n + k];
+            if (dik == OR_INF64) continue;
+            for (uint32_t j = 0; j < n; j++) {
+                const uint64_t dkj = D[(size_t)k * n + j];
+                if (dkj == OR_INF64) continue;
+                if (dik + dkj < D[(size_t)i * n + j]) D[(size_t)i * n + j] = dik + dkj;
+            }
+        }
     return 0;
 }

@@ -6,7 +6,8 @@
     python -m paper_2404_17101_gb300 scc   --input g.adj [--directed] [--out labels.u32]
     python -m paper_2404_17101_gb300 bfs64 --input g.adj [--sources ...] [--out dist.u32]
 
-`--input` reads the PBBS "AdjacencyGraph" text format; `--workload` takes a
+`--input` reads the PBBS "AdjacencyGraph" text format, or the GBBS binary
+layout when the file name ends in `.bin`; `--workload` takes a
 named generator of the graphgen module instead (e.g. knn_10m, grid_1000).
 One JSON line with the device time (kernel events), rounds and, for BFS, the
 traversed edges and GTEPS is printed; `--out` writes the result as raw
@@ -34,7 +35,7 @@ def _args(argv):
                                  description="Exact BFS, reachability and SCC on one GB300.")
     ap.add_argument("op", choices=["bfs", "reach", "scc", "bfs64"])
     src = ap.add_mutually_exclusive_group(required=True)
-    src.add_argument("--input", help="graph in the PBBS AdjacencyGraph text format")
+    src.add_argument("--input", help="graph file: PBBS AdjacencyGraph text, or GBBS binary (*.bin)")
     src.add_argument("--workload", help="named graphgen generator, e.g. knn_10m, grid_1000, dgrid_4000")
     ap.add_argument("--directed", action="store_true", help="arcs as given (else the file is symmetric)")
     ap.add_argument("--source", type=int, default=0, help="bfs: source vertex")
@@ -56,7 +57,8 @@ def main(argv=None) -> int:
     import graphgen as gg
     import paper_2404_17101_gb300 as pg
     if a.input:
-        g = gg.read_adj(a.input, directed=a.directed)
+        reader = gg.read_gbbs_bin if a.input.endswith(".bin") else gg.read_adj
+        g = reader(a.input, directed=a.directed)
     else:
         if not hasattr(gg, a.workload):
             print(f"error: unknown workload {a.workload!r}", file=sys.stderr)

@@ -57,3 +57,15 @@ def test_bfs_reach_scc_on_a_file(tmp_path):
     assert r.returncode == 0, r.stderr
     D = np.fromfile(out, dtype="<u4").reshape(3, g.n)
     assert np.array_equal(D, oracle.bfs_multi(g, np.array([3, 77, 1000], dtype=np.uint32)))
+
+
+@pytest.mark.gpu
+def test_bfs_on_a_gbbs_binary_file(tmp_path):
+    """The same command line on a GBBS binary file (*.bin) against the oracle."""
+    g = gg.dgrid(40, 70, 8, shortcuts=4)
+    p = str(tmp_path / "g.bin")
+    gg.write_gbbs_bin(g, p)
+    out = str(tmp_path / "d.u32")
+    r = _run(["bfs", "--input", p, "--directed", "--source", "11", "--out", out])
+    assert r.returncode == 0, r.stderr
+    assert np.array_equal(np.fromfile(out, dtype="<u4"), oracle.bfs(g, 11))
