@@ -56,6 +56,8 @@ def parse_args():
     ap.add_argument("--configs", action="store_true",
                     help="instead of the headline line: one JSON line per benchmark configuration")
     ap.add_argument("--with-strip", action="store_true", help="--configs: include the 1 x 20M strip")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the other configurations' forms (C1, C3, C4, C5) in the headline line")
     return ap.parse_args()
 
 
@@ -187,6 +189,206 @@ def cpu_baseline_bfs(g, src, budget_s=12.0):
         ts.append(time.perf_counter() - t0)
     n_r, m_r = oracle.reached_edges(g, d)
     return d, n_r, m_r, ts
+
+
+def eccentricity(out):
+    """Largest finite distance in a device int32 view of uint32 distances."""
+    import torch
+    d = out.to(torch.int64) & 0xFFFFFFFF
+    fin = d[d != 0xFFFFFFFF]
+    return int(fin.max().item()) if fin.numel() else 0
+
+
+def latency_floor(pg, gg, rounds, levels, kernel_ms):
+    """The round-latency floor of a traversal with `rounds` rounds over
+    `levels` dependent BFS levels: rounds x t_barrier + levels x t_hop.
+    t_barrier: an empty persistent loop of grid barriers (pg_probe_barrier);
+    t_hop: the per-level cost of a one-vertex-per-level chain, measured as
+    a BFS on a 1 x 20,000 strip (tau = 64) minus its barriers."""
+    t_bar = pg.probe_barrier(20000)
+    strip = gg.strip(20000)
+    S = pg.Graph.from_graphgen(strip, ell=True)
+    cfg = pg.default_config(tau=64)
+    st = pg.Stats()
+    for _ in range(2):
+        S.bfs(0, cfg=cfg, stats=st)
+    ts = []
+    for _ in range(3):
+        S.bfs(0, cfg=cfg, stats=st)
+        ts.append(st.kernel_ms)
+    S.free()
+    t_hop = (min(ts) * 1e3 - st.rounds * t_bar) / (strip.n - 1)
+    floor_ms = (rounds * t_bar + levels * t_hop) / 1e3
+    return {"t_barrier_us": t_bar, "t_hop_us": t_hop, "rounds": rounds, "levels": levels,
+            "floor_ms": floor_ms, "frac_latency": floor_ms / kernel_ms,
+            "how": "t_barrier: pg_probe_barrier, 20000 empty grid barriers of the traversal's "
+                   "launch shape; t_hop: BFS on a 1x20000 strip at tau 64, minus its rounds' "
+                   "barriers, per level"}
+
+
+def other_configs(pg, gg, peak, steps, warm, with_oracle):
+    """Timed forms of the other benchmark configurations (one GPU):
+    C3 (R-MAT 24, 64 single-source BFS vs one 64-source batch), C4 (directed
+    4000^2 grid, 64-source forward + backward reachability batch vs single
+    launches, default and autotuned), C1 (grid 1000^2) and C5 (held-out kNN
+    30M, k = 3): plain tau = 16 vs the best fixed tau vs the learned
+    schedule.  Device times are kernel events (min of `steps` after `warm`
+    warm-ups, L2 flushed between runs).  With `with_oracle` the CPU leg runs
+    the oracle on a bounded sample (sampled rows / bits) of every form's
+    output and reports whether they are equal, and the oracle's time."""
+    import numpy as np
+    import torch
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")
+    w = pg.trained_weights()
+    res = {}
+
+    def best(call, reps=steps, wu=warm):
+        st = pg.Stats()
+        for _ in range(wu):
+            call(st)
+        ts = []
+        for i in range(reps):
+            flush.fill_(i)
+            call(st)
+            ts.append(st.kernel_ms)
+        return min(ts), st
+
+    # ---- C3: 64 single-source BFS vs one 64-source batch
+    t0 = time.perf_counter()
+    g = gg.rmat_24()
+    t_gen = time.perf_counter() - t0
+    G = pg.Graph.from_graphgen(g)
+    srcs = gg.pick_sources(g, 64, 3)
+    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    c1 = pg.default_config(tau=1, direction=pg.PG_DIR_AUTO)
+    single, m_tot, rows = 0.0, 0, {}
+    keep = (0, 17)
+    for j, s_ in enumerate(srcs):
+        ms, _ = best(lambda st: G.bfs(int(s_), out=out, cfg=c1, stats=st), 1, 1 if j == 0 else 0)
+        single += ms
+        m_tot += G.count_reached(out)[1]
+        if j in keep:
+            rows[j] = pg.to_uint32(out)
+    D = torch.empty((64, g.n), dtype=torch.int32, device="cuda")
+    cb = pg.default_config(direction=pg.PG_DIR_AUTO)
+    ms_b, st_b = best(lambda st: G.bfs_multi(srcs, cfg=cb, stats=st, out=D))
+    B3 = 4 * (g.n + 1) + 4 * g.m + 4 * 64 * g.n
+    c3 = {"n": g.n, "m": g.m, "k": 64, "traversed_edges_sum": m_tot, "generate_s": t_gen,
+          "single_x64": {"ms": single, "gteps": m_tot / single / 1e6,
+                         "form": "64 pg_bfs calls, tau 1, push/pull (Beamer)"},
+          "batch64": {"ms": ms_b, "gteps": m_tot / ms_b / 1e6, "rounds": st_b.rounds,
+                      "pull_rounds": st_b.pull_rounds,
+                      "roofline": {"bound": "hbm", "algorithmic_bytes": B3,
+                                   "achieved": B3 / (ms_b * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                                   "frac": B3 / (ms_b * 1e-3) / 1e9 / peak,
+                                   "bytes": "4(n+1) + 4m + 4kn"}},
+          "batch_speedup": single / ms_b}
+    if with_oracle:
+        import oracle
+        Dh = {j: pg.to_uint32(D[j]) for j in keep}
+        t0 = time.perf_counter()
+        want = {j: oracle.bfs(g, int(srcs[j])) for j in keep}
+        t_or = (time.perf_counter() - t0) / len(keep)
+        c3["exact_vs_oracle"] = {
+            "rows": list(keep),
+            "batch": all(np.array_equal(Dh[j], want[j]) for j in keep),
+            "single": all(np.array_equal(rows[j], want[j]) for j in keep)}
+        c3["cpu_oracle"] = {"ms": 64 * t_or * 1e3, "gteps": m_tot / (64 * t_or) / 1e9, "cores": 1,
+                            "sample": f"{len(keep)} sources timed, times 32"}
+    res["C3 rmat_24"] = c3
+    del G, D, rows
+    torch.cuda.empty_cache()
+
+    # ---- C4: 64-source forward + backward reachability in one launch
+    g = gg.dgrid_4000()
+    G = pg.Graph.from_graphgen(g, ell=True)
+    srcs = gg.pick_sources(g, 64, 4)
+    both = pg.PG_FWD | pg.PG_BWD
+    ms_d, st_d = best(lambda st: G.reach_multi(srcs, both, cfg=pg.default_config(), stats=st))
+    t0 = time.perf_counter()
+    tuned = G.autotune(srcs, kind=1, direction=both, trials=2)
+    t_tune = time.perf_counter() - t0
+    fw_bw = {}
+
+    def run_tuned(st):
+        fw_bw["r"] = G.reach_multi(srcs, both, cfg=tuned, stats=st)
+    ms_t, st_t = best(run_tuned)
+    fw, bw = fw_bw["r"]
+    single = 0.0
+    for s_ in srcs[:8]:
+        ms, _ = best(lambda st: G.reach_multi([int(s_)], both, cfg=pg.default_config(), stats=st), 1, 1)
+        single += ms
+    single *= 8
+    f, b = pg.to_uint64(fw), pg.to_uint64(bw)
+    deg = np.diff(g.offsets.astype(np.int64))
+    tdeg = np.bincount(g.indices, minlength=g.n).astype(np.int64)
+    nr_f, nr_b = int(np.count_nonzero(f)), int(np.count_nonzero(b))
+    mr_f, mr_b = int(deg[f != 0].sum()), int(tdeg[b != 0].sum())
+    B4 = (4 * (nr_f + 1) + 4 * mr_f + 8 * g.n) + (4 * (nr_b + 1) + 4 * mr_b + 8 * g.n)
+    c4 = {"n": g.n, "m": g.m, "k": 64,
+          "batch64_default": {"ms": ms_d, "rounds": st_d.rounds},
+          "batch64_tuned": {"ms": ms_t, "rounds": st_t.rounds, "tau": int(tuned.tau),
+                            "chunk": int(tuned.chunk), "local_queue": int(tuned.local_queue),
+                            "cta_queue": int(tuned.cta_queue), "vgc_mode": int(tuned.vgc_mode),
+                            "blocks_per_sm": int(tuned.blocks_per_sm), "autotune_s": t_tune,
+                            "roofline": {"bound": "hbm", "algorithmic_bytes": B4,
+                                         "achieved": B4 / (ms_t * 1e-3) / 1e9, "peak": peak,
+                                         "unit": "GB/s", "frac": B4 / (ms_t * 1e-3) / 1e9 / peak,
+                                         "bytes": "per direction 4(n_r+1) + 4 m_r + 8n"}},
+          "single_x64": {"ms": single, "sample": "8 sources timed, times 8"},
+          "batch_speedup": single / ms_t}
+    if with_oracle:
+        import oracle
+        sample = np.array([3, 40], dtype=np.int64)
+        t0 = time.perf_counter()
+        wf = oracle.reach(g, srcs[sample])
+        t_or = (time.perf_counter() - t0) / len(sample)
+        wb = oracle.reach(g, srcs[sample], backward=True)
+        ok = True
+        for i, j in enumerate(sample):
+            bit, bi = np.uint64(1) << np.uint64(j), np.uint64(1) << np.uint64(i)
+            ok &= bool(np.array_equal((f & bit) != 0, (wf & bi) != 0))
+            ok &= bool(np.array_equal((b & bit) != 0, (wb & bi) != 0))
+        c4["exact_vs_oracle"] = {"bits": sample.tolist(), "fwd_and_bwd": ok}
+        c4["cpu_oracle"] = {"ms": 128 * t_or * 1e3, "cores": 1,
+                            "sample": "2 sources, forward, timed; times 128"}
+    res["C4 dgrid_4000"] = c4
+    del G
+    torch.cuda.empty_cache()
+
+    # ---- C1 and C5 held-out kNN: plain tau 16, tau 64, learned
+    for name, make in (("C1 grid_1000", gg.grid_1000), ("C5 knn_30m_k3", gg.knn_30m_k3)):
+        g = make()
+        G = pg.Graph.from_graphgen(g, ell=True)
+        forms = {"plain_tau16": pg.default_config(), "plain_tau64": pg.default_config(tau=64)}
+        if w is not None:
+            G.set_schedule_weights(w)
+            forms["learned"] = pg.default_config(schedule=pg.PG_SCHED_LEARNED)
+        outs, fr = {}, {}
+        for f_, cfg in forms.items():
+            o = torch.empty(g.n, dtype=torch.int32, device="cuda")
+            ms, st = best(lambda st: G.bfs(0, out=o, cfg=cfg, stats=st))
+            outs[f_] = o
+            fr[f_] = {"ms": ms, "rounds": st.rounds}
+        n_r, m_r = G.count_reached(outs["plain_tau16"])
+        for f_ in fr:
+            fr[f_]["gteps"] = m_r / fr[f_]["ms"] / 1e6
+        Bc = algorithmic_bytes(g.n, n_r, m_r)
+        entry = {"n": g.n, "m": g.m, "traversed_edges": m_r, "forms": fr,
+                 "algorithmic_bytes": Bc}
+        if with_oracle:
+            import oracle
+            t0 = time.perf_counter()
+            want = oracle.bfs(g, 0)
+            t_or = time.perf_counter() - t0
+            entry["exact_vs_oracle"] = {f_: bool(np.array_equal(pg.to_uint32(o), want))
+                                        for f_, o in outs.items()}
+            entry["cpu_oracle"] = {"ms": t_or * 1e3, "gteps": m_r / t_or / 1e9, "cores": 1,
+                                   "sample": "full workload, one run"}
+        res[name] = entry
+        del G, outs
+        torch.cuda.empty_cache()
+    return res
 
 
 def run_reference(args):
@@ -401,6 +603,7 @@ def main():
 
     G.bfs(src, out=out, cfg=plain_cfg)
     n_r, m_r = G.count_reached(out)
+    levels = eccentricity(out)
     B = algorithmic_bytes(g.n, n_r, m_r)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")  # 256 MB > L2
 
@@ -490,6 +693,11 @@ def main():
                "d2h_bytes_per_step": 4 * g.n, "steps": nsteps,
                "ms_per_step": emean * 1e3}
 
+    floor = latency_floor(pg, gg, int(round(statistics.mean(R["rounds"]))), levels, kmean)
+    extra = None
+    if world == 1 and not args.no_extra:
+        extra = other_configs(pg, gg, peak, steps=3, warm=2, with_oracle=not args.no_cpu_baseline)
+
     if rank == 0:
         def summary(r):
             return {"gteps": m_r * len(r["ms"]) / (sum(r["ms"]) * 1e6),
@@ -512,13 +720,15 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "pg_traverse_kernel<BFS>", "algorithmic_bytes": B,
-                         "kernel_ms_mean": kmean},
+                         "kernel_ms_mean": kmean, "latency_floor": floor},
+            "gteps_graph500": value / 2,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": args.steps,
             "clocks": R["clocks"],
             "exact_vs_oracle": exact,
             "forms": {k: summary(v) for k, v in results.items()},
+            "other_configs": extra,
         }
         print(json.dumps(line), flush=True)
     if dist:

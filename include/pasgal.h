@@ -124,7 +124,7 @@ typedef struct pg_config {
     uint32_t test_stall_block;  /* fault injection: this CTA never arrives at the grid barrier; 0xFFFFFFFF = off */
     uint32_t vgc_mode;          /* local search for tau > 1: PG_VGC_CTA (default) or PG_VGC_WARP */
     uint32_t cta_queue;         /* PG_VGC_CTA: vertices per level a CTA keeps locally (64..8192); 0 = 2048 */
-    uint32_t reserved;
+    uint32_t delta;             /* pg_sssp: step width of a round's distance threshold; 0 = 8 x mean weight */
     const uint8_t *script;      /* host: action per round for PG_SCHED_SCRIPT (round i uses script[i % len]) */
     pg_round_trace *trace_out;  /* host buffer for per-round records, or NULL */
     const uint32_t *ref_dist;   /* device: known final distances (training traces), or NULL */
@@ -220,8 +220,8 @@ pg_status pg_bfs_multi(pg_graph *g, const uint32_t *sources, uint32_t k, uint32_
  *  label_out:  n uint32, device or host memory; label_out[v] = the smallest
  *              vertex id of v's SCC (deterministic, independent of cfg).
  *  cfg:        tau (hop window of the local search), threads_per_block,
- *              local_queue, timeout_ms (per wait) and seed (pivot
- *              priorities) are used; NULL = defaults.
+ *              local_queue, timeout_ms (per wait), seed (pivot priorities)
+ *              and test_stall_block are used; NULL = defaults.
  *  stats:      rounds = search rounds summed over iterations, expansions =
  *              vertices expanded, kernel_ms = the whole computation; NULL ok.
  *  iterations: number of pivot iterations (NULL ok).
@@ -231,6 +231,33 @@ pg_status pg_bfs_multi(pg_graph *g, const uint32_t *sources, uint32_t k, uint32_
  */
 pg_status pg_scc(pg_graph *g, uint32_t *label_out, const pg_config *cfg, pg_stats *stats,
                  uint32_t *iterations, void *stream);
+
+/*
+ * Arc weights for pg_sssp: weights[e] (uint32) is the weight of arc e of the
+ * forward CSR (m entries, host or device memory, copied).  Replaces earlier
+ * weights.  Errors: NULL -> PG_ERR_INVALID_ARG; allocation -> PG_ERR_CUDA.
+ */
+pg_status pg_graph_set_weights(pg_graph *g, const uint32_t *weights, void *stream);
+
+/*
+ * Single-source shortest paths (Sec. 2.2, parallel SSSP on the stepping
+ * framework with VGC and frontier bags): dist_out[v] = the smallest sum of
+ * arc weights over paths src -> v (uint64), 0xFFFFFFFFFFFFFFFF if v is
+ * unreachable.  Needs pg_graph_set_weights.  A round expands the frontier
+ * entries below L + delta (L = the frontier's smallest tentative distance;
+ * cfg->delta, 0 = 8 x the mean weight) and keeps the others; a warp's local
+ * search expands its own improvements below the threshold (up to
+ * cfg->tau x 32 per task) and queues the rest.  The result is exact for
+ * every delta and tau.
+ *  dist_out: n uint64, device or host memory.  cfg: tau, delta,
+ *  threads_per_block, blocks_per_sm, local_queue, timeout_ms, max_rounds,
+ *  test_stall_block are used; NULL = defaults.  stats: rounds, expansions,
+ *  pushes, kernel_ms.
+ *  Errors: src >= n, NULL, no weights -> PG_ERR_INVALID_ARG; device wait
+ *  over timeout_ms -> PG_ERR_TIMEOUT (dist undefined).
+ */
+pg_status pg_sssp(pg_graph *g, uint32_t src, uint64_t *dist_out, const pg_config *cfg,
+                  pg_stats *stats, void *stream);
 
 /*
  * Traversed-edge count for TEPS: *n_reached = #{v : dist[v] != 0xFFFFFFFF},
@@ -298,6 +325,20 @@ pg_status pg_autotune(pg_graph *g, uint32_t kind, const uint32_t *sources, uint3
 #define PG_NOALLOC_SCRATCH_BYTES (13u << 20)
 pg_status pg_bfs_noalloc(const uint32_t *offsets, const uint32_t *indices, uint32_t n, uint32_t m,
                          uint32_t src, uint32_t *dist_out, const pg_config *cfg, void *stream);
+
+/*
+ * Round-barrier latency probe.  Every round of Algorithm 1 ends with a
+ * grid-wide barrier, so a traversal of R rounds takes at least R barrier
+ * latencies.  This runs the traversal's persistent launch shape
+ * (blocks_per_sm CTAs per SM, 0 = 1; threads_per_block, 0 = 512) through
+ * `rounds` (1..2^24) grid barriers with no other work and writes the mean
+ * time per barrier in microseconds (CUDA events) to *us_per_barrier.
+ * Allocates and frees a 1 KB control block on `stream`; synchronous.
+ * Errors: PG_ERR_INVALID_ARG (bad sizes, NULL), PG_ERR_TIMEOUT (a barrier
+ * wait exceeded 5 s), PG_ERR_CUDA.
+ */
+pg_status pg_probe_barrier(uint32_t rounds, uint32_t threads_per_block, uint32_t blocks_per_sm,
+                           float *us_per_barrier, void *stream);
 
 /* Thread-local message for the last failing call on this thread ("" if none). */
 const char *pg_last_error(void);

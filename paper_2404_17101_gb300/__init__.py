@@ -37,7 +37,8 @@ INF = 0xFFFFFFFF
 EXPORTS = ["pg_config_default", "pg_graph_upload", "pg_graph_set_transpose", "pg_graph_free",
            "pg_graph_info", "pg_bfs", "pg_reach_multi", "pg_bfs_multi", "pg_count_reached",
            "pg_set_schedule_weights", "pg_mlp_forward", "pg_mlp_backward", "pg_mlp_adam",
-           "pg_autotune", "pg_bfs_noalloc", "pg_scc", "pg_last_error", "pg_version"]
+           "pg_autotune", "pg_bfs_noalloc", "pg_scc", "pg_probe_barrier", "pg_graph_set_weights",
+           "pg_sssp", "pg_last_error", "pg_version"]
 NOALLOC_MAX_N = 1 << 20
 
 
@@ -65,7 +66,7 @@ class Config(ctypes.Structure):
                 ("max_rounds", ctypes.c_uint32), ("seed", ctypes.c_uint32),
                 ("script_len", ctypes.c_uint32), ("trace_cap", ctypes.c_uint32),
                 ("test_stall_block", ctypes.c_uint32), ("vgc_mode", ctypes.c_uint32),
-                ("cta_queue", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("cta_queue", ctypes.c_uint32), ("delta", ctypes.c_uint32),
                 ("script", ctypes.c_void_p), ("trace_out", ctypes.POINTER(RoundTrace)),
                 ("ref_dist", ctypes.c_void_p)]
 
@@ -112,6 +113,9 @@ def load(path: str | None = None):
         "pg_autotune": (ctypes.c_int, [vp, u32, vp, u32, u32, u32, P(Config), vp]),
         "pg_bfs_noalloc": (ctypes.c_int, [vp, vp, u32, u32, u32, vp, P(Config), vp]),
         "pg_scc": (ctypes.c_int, [vp, vp, P(Config), P(Stats), P(u32), vp]),
+        "pg_probe_barrier": (ctypes.c_int, [u32, u32, u32, P(ctypes.c_float), vp]),
+        "pg_graph_set_weights": (ctypes.c_int, [vp, vp, vp]),
+        "pg_sssp": (ctypes.c_int, [vp, u32, vp, P(Config), P(Stats), vp]),
         "pg_last_error": (ctypes.c_char_p, []),
         "pg_version": (ctypes.c_char_p, []),
     }
@@ -263,6 +267,33 @@ class Graph:
                              ctypes.byref(stats) if stats else None, ctypes.byref(it), _stream_ptr(stream)))
         return out, it.value
 
+    def set_weights(self, weights, stream=None):
+        """Arc weights for sssp: uint32, one per arc of the forward CSR (numpy
+        or CUDA tensor)."""
+        p, keep = _u32_array(weights)
+        n_w = keep.numel() if hasattr(keep, "numel") else len(keep)
+        if n_w != self.m:
+            raise ValueError(f"set_weights: {n_w} weights for {self.m} arcs")
+        _check(load().pg_graph_set_weights(self._h, p, _stream_ptr(stream)))
+
+    def sssp(self, src: int, out=None, cfg: Config | None = None, stats: Stats | None = None,
+             stream=None):
+        """Shortest-path distances from src (needs set_weights); returns a CUDA
+        int64 tensor holding uint64 bits (0xFFFFFFFFFFFFFFFF: unreachable)."""
+        import torch
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.int64, device="cuda")
+        if isinstance(out, torch.Tensor):
+            if out.dtype != torch.int64 or not out.is_contiguous() or out.numel() != self.n:
+                raise ValueError("sssp: out must be a contiguous int64 tensor of n entries")
+            ptr = ctypes.c_void_p(out.data_ptr())
+        else:
+            assert out.dtype == np.uint64 and out.flags.c_contiguous and len(out) == self.n
+            ptr = ctypes.c_void_p(out.ctypes.data)
+        _check(load().pg_sssp(self._h, int(src), ptr, ctypes.byref(cfg) if cfg else None,
+                              ctypes.byref(stats) if stats else None, _stream_ptr(stream)))
+        return out
+
     def count_reached(self, dist, stream=None):
         a, b = ctypes.c_uint64(), ctypes.c_uint64()
         _check(load().pg_count_reached(self._h, ctypes.c_void_p(dist.data_ptr()), ctypes.byref(a),
@@ -359,6 +390,16 @@ def bfs_noalloc(offsets, indices, src: int, out, cfg: Config | None = None, stre
                                      int(src), ctypes.c_void_p(out.data_ptr()),
                                      ctypes.byref(cfg) if cfg else None, _stream_ptr(stream)))
     return out
+
+
+def probe_barrier(rounds: int = 20000, threads_per_block: int = 0, blocks_per_sm: int = 0,
+                  stream=None) -> float:
+    """Microseconds per grid barrier of an empty persistent loop on the
+    current device (the per-round floor of any traversal)."""
+    us = ctypes.c_float()
+    _check(load().pg_probe_barrier(int(rounds), int(threads_per_block), int(blocks_per_sm),
+                                   ctypes.byref(us), _stream_ptr(stream)))
+    return float(us.value)
 
 
 def version() -> str:

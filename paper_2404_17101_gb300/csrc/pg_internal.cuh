@@ -109,10 +109,18 @@ __device__ __forceinline__ unsigned pg_ld_relaxed(const unsigned *p) {
     return v;
 }
 
-__device__ __forceinline__ bool pg_grid_sync(PgCtrl *c, unsigned nblocks, unsigned &gen,
-                                             unsigned long long timeout_ns, int *s_flag) {
+// pg_grid_sync_then: the same barrier, with `pre()` run by thread 0 after the
+// CTA's threads have all arrived and before the CTA's arrival is released,
+// so that per-CTA aggregates (built in shared memory during the round) reach
+// global memory with one atomic per CTA and are visible to every CTA after
+// the barrier, at no extra CTA barrier.
+template <class Pre>
+__device__ __forceinline__ bool pg_grid_sync_then(PgCtrl *c, unsigned nblocks, unsigned &gen,
+                                                  unsigned long long timeout_ns, int *s_flag,
+                                                  Pre pre) {
     __syncthreads();
     if (threadIdx.x == 0) {
+        pre();
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&c->bar_cnt) : "memory");
         const unsigned target = (gen + 1u) * nblocks;
         const unsigned long long t0 = pg_gtimer();
@@ -132,6 +140,11 @@ __device__ __forceinline__ bool pg_grid_sync(PgCtrl *c, unsigned nblocks, unsign
     gen++;
     __syncthreads();
     return *s_flag == 0;
+}
+
+__device__ __forceinline__ bool pg_grid_sync(PgCtrl *c, unsigned nblocks, unsigned &gen,
+                                             unsigned long long timeout_ns, int *s_flag) {
+    return pg_grid_sync_then(c, nblocks, gen, timeout_ns, s_flag, [] {});
 }
 
 // ------------------------------------------------------------ host side
@@ -155,7 +168,9 @@ int pg_device_sms(int dev);
 
 struct PgMsbfsWork;  // batched BFS buffers (pg_msbfs.cu)
 struct PgSccWork;    // SCC buffers (pg_scc.cu)
+struct PgSsspWork;   // arc weights and SSSP counters (pg_sssp.cu)
 void pg_scc_release(pg_graph *g);
+void pg_sssp_release(pg_graph *g);
 void pg_msbfs_release(pg_graph *g);  // frees them; rebuilt on the next batched call
 
 struct pg_graph {
@@ -186,6 +201,7 @@ struct pg_graph {
     bool has_weights;
     PgMsbfsWork *msbfs;
     PgSccWork *scc;
+    PgSsspWork *sssp;
     int num_sms;
     cudaEvent_t ev0, ev1;  // bracket the traversal kernel of the last call
 };

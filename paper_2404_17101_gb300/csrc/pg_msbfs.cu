@@ -1,13 +1,33 @@
 // pg_msbfs.cu -- batched BFS from up to 64 sources (pg_bfs_multi).
 //
 // All k searches share every round of Algorithm 1: a vertex carries one bit
-// per source in three uint64 words (seen, visit = reached in the last
-// round, next).  A round is either top-down (each vertex with visit != 0
-// ORs its bits into its out-neighbours' next) or bottom-up (each vertex
-// still missing bits ORs the visit words of its in-neighbours, stopping as
-// soon as every missing bit is found), chosen with the direction-
-// optimisation test of [Beamer12] (Sec. 2.2).  A bit that first appears at a
-// vertex in round L gives that source's hop distance L + 1 (Sec. 2.2).
+// per source in uint64 words (seen; visit = reached in the last round, two
+// buffers by round parity; next = bits arriving this round).  A round is
+// either top-down (the frontier's vertices OR their visit bits into their
+// out-neighbours' next) or bottom-up (every vertex still missing bits ORs the
+// visit words of its in-neighbours, stopping as soon as every missing bit is
+// found), chosen with the direction-optimisation test of [Beamer12]
+// (Sec. 2.2).  A bit that first appears at a vertex in round L gives that
+// source's hop distance L + 1 (Sec. 2.2).
+//
+// No round sweeps the whole vertex set:
+//  - a top-down round expands the frontier list (the vertices that gained
+//    bits in the previous round); every vertex whose next word it turns
+//    non-zero is listed once ("touched"), and only those are updated;
+//  - a bottom-up round walks the list of unfinished vertices (seen != all
+//    bits; every vertex before the first bottom-up round) and updates each
+//    vertex in place: its new bits go to the other visit buffer, so the
+//    round's gathers still read the previous round's bits; the still
+//    unfinished vertices form the next such list.
+//  A visit word that was not rewritten in the last round holds bits of an
+//  older round; their sources already reached every out-neighbour, so the
+//  "missing bits" masks filter them and no clearing is needed.
+// Distances are kept as 5 bit-planes per vertex (plane b, bit j = bit b of
+// the distance of source j), updated only for the bits that arrive; one
+// decode pass after the last round writes the k x n source-major output with
+// coalesced stores (and 0xFFFFFFFF where the bit never arrived).  A bit that
+// arrives in round 31 or later is written to the output at once and marked
+// with the plane code 31, which the decode pass skips.
 //
 // High-degree splitting (the load balance of Sec. 2.1's small-task
 // discussion): a vertex with at least kHeavy edges in a direction is never
@@ -15,25 +35,44 @@
 // at most kChunk edges, listed once per graph, and any warp takes a chunk:
 // top-down ORs the vertex's bits into the chunk's targets, bottom-up ORs the
 // chunk's visit words (32 at a time, stopping once every missing bit is
-// found) and merges them into next[w] with one atomicOr.
+// found) into next[w] with one atomicOr, and a short pass over the heavy
+// vertices then updates them.
 #include "pg_internal.cuh"
 
 namespace {
 constexpr uint32_t kHeavy = 32;    // edges: below, one thread (bottom-up) / one lane (top-down)
 constexpr uint32_t kChunk = 1024;  // edges per chunk of a heavy vertex
 constexpr uint32_t kGather = 8;    // bottom-up: in-neighbour gathers in flight per light vertex
+constexpr uint32_t kPlanes = 5;    // distance bit-planes: distances 0..30, code 31 = written directly
+constexpr uint32_t kDirect = (1u << kPlanes) - 1u;
 }  // namespace
 
+// Per-round list sizes; round r reads slot r % 4 and fills slot (r + 1) % 4.
+struct MsCount {
+    unsigned F;               // frontier list size
+    unsigned T;               // touched list size (top-down rounds)
+    unsigned U;               // unfinished list size (bottom-up rounds)
+    unsigned pad;
+    unsigned long long E;     // out-degree sum of the frontier
+    unsigned long long pad2[2];
+};
+
 struct PgMsbfsWork {
-    unsigned long long *seen, *visit, *next;
+    unsigned long long *seen, *visit[2], *next;
+    unsigned long long *planes;  // [kPlanes][n]
+    uint32_t *front[2], *unfin[2], *touched;
+    uint32_t *flev;              // round whose frontier a vertex last joined (its visit word's age)
+    MsCount *cnt;                // [4]
     uint32_t n;
-    uint2 *chunks[2];     // (vertex, first edge) per chunk: out-lists, in-lists
+    uint2 *chunks[2];            // (vertex, first edge) per chunk: out-lists, in-lists
     uint32_t nchunks[2];
 };
 
 void pg_msbfs_release(pg_graph *g) {
     if (g && g->msbfs) {
         cudaFree(g->msbfs->seen);
+        cudaFree(g->msbfs->front[0]);
+        cudaFree(g->msbfs->cnt);
         cudaFree(g->msbfs->chunks[0]);
         if (g->msbfs->chunks[1] != g->msbfs->chunks[0]) cudaFree(g->msbfs->chunks[1]);
         delete g->msbfs;
@@ -73,7 +112,10 @@ struct MsArgs {
     const uint2 *chunks_out, *chunks_in;
     uint32_t nchunks_out, nchunks_in;
     PgCtrl *ctrl;
-    unsigned long long *seen, *visit, *next;
+    MsCount *cnt;
+    unsigned long long *seen, *visit0, *visit1, *next, *planes;
+    uint32_t *front0, *front1, *unfin0, *unfin1, *touched;
+    uint32_t *flev;
     uint32_t *dist;       // k * n, source-major
     uint32_t k;
     uint32_t sources[64];
@@ -86,6 +128,36 @@ __device__ __forceinline__ unsigned long long wsum(unsigned long long x) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
     return x;
+}
+
+// Warp-collective append of the lanes' `go` ids to list[] with one atomic on
+// *size; returns nothing (the list capacity is n, and every id is appended at
+// most once per round, so it cannot overflow).
+__device__ __forceinline__ void list_append(uint32_t *list, unsigned *size, bool go, uint32_t id,
+                                            int lane) {
+    const unsigned bal = __ballot_sync(kFull, go);
+    if (!bal) return;
+    uint32_t pos = 0;
+    if (lane == 0) pos = atomicAdd(size, (unsigned)__popc(bal));
+    pos = __shfl_sync(kFull, pos, 0);
+    if (go) list[pos + __popc(bal & pg_lanemask_lt())] = id;
+}
+
+// New bits nb of vertex w at distance dnew: visit word of the next round,
+// distance planes (or the output directly from round 31 on).
+__device__ __forceinline__ void record_bits(const MsArgs &A, unsigned long long *visit_nxt, uint32_t w,
+                                            unsigned long long nb, uint32_t dnew) {
+    visit_nxt[w] = nb;
+    A.flev[w] = dnew;
+    const uint32_t n = A.G.n;
+    const uint32_t code = dnew >= kDirect ? kDirect : dnew;
+#pragma unroll
+    for (uint32_t b = 0; b < kPlanes; b++)
+        if ((code >> b) & 1u) A.planes[(size_t)b * n + w] |= nb;
+    if (code == kDirect) {
+        for (uint32_t j = 0; j < A.k; j++)
+            if ((nb >> j) & 1ull) A.dist[(size_t)j * n + w] = dnew;
+    }
 }
 
 __global__ void __launch_bounds__(512) pg_msbfs_kernel(const MsArgs A) {
@@ -102,52 +174,58 @@ __global__ void __launch_bounds__(512) pg_msbfs_kernel(const MsArgs A) {
     PgCtrl *ctrl = A.ctrl;
     unsigned gen = 0;
 
-    // init: sources at distance 0
-    unsigned long long fv = 0, fe = 0;
+    // init: sources at distance 0 (all-zero planes), every other word 0
     for (uint32_t v = gtid; v < n; v += gthreads) {
         unsigned long long b = 0;
         for (uint32_t j = 0; j < k; j++)
             if (A.sources[j] == v) b |= 1ull << j;
         A.seen[v] = b;
-        A.visit[v] = b;
+        A.visit0[v] = b;
+        A.visit1[v] = 0;
         A.next[v] = 0;
-        for (uint32_t j = 0; j < k; j++)
-            if ((b >> j) & 1ull) A.dist[(size_t)j * n + v] = 0;
-        if (b) { fv++; fe += A.G.off[v + 1] - A.G.off[v]; }
+        A.flev[v] = 0;
+        for (uint32_t p = 0; p < kPlanes; p++) A.planes[(size_t)p * n + v] = 0;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        for (int s = 0; s < PG_NUM_SLOTS; s++) {
-            ctrl->slot[s].size = 0;
-            ctrl->slot[s].out_edges = 0;
+    if (gtid == 0) {
+        // the first frontier: the distinct sources
+        uint32_t F = 0;
+        unsigned long long E = 0;
+        for (uint32_t j = 0; j < k; j++) {
+            const uint32_t v = A.sources[j];
+            bool dup = false;
+            for (uint32_t i = 0; i < j; i++) dup |= (A.sources[i] == v);
+            if (dup) continue;
+            A.front0[F++] = v;
+            E += A.G.off[v + 1] - A.G.off[v];
         }
-    if (A.stall_block == blockIdx.x) return;
-    if (!pg_grid_sync(ctrl, gridDim.x, gen, A.timeout_ns, &s_flag)) return;
-    fv = wsum(fv);
-    fe = wsum(fe);
-    if (lane == 0 && fv) {
-        atomicAdd(&ctrl->slot[0].size, (unsigned)fv);
-        atomicAdd(&ctrl->slot[0].out_edges, fe);
+        A.cnt[0].F = F;
+        A.cnt[0].E = E;
     }
+    if (A.stall_block == blockIdx.x) return;  // fault injection: never arrive
     if (!pg_grid_sync(ctrl, gridDim.x, gen, A.timeout_ns, &s_flag)) return;
 
     unsigned long long edges_seen = 0;
     const unsigned long long t_deadline = pg_gtimer() + 16ull * A.timeout_ns;
     bool bottom_up = false;
+    bool uall = true;          // no bottom-up round yet: every vertex is unfinished
+    uint32_t up = 0, Ucur = 0; // current unfinished list and its size
     uint32_t L = 0, pulls = 0;
     for (;; L++) {
-        PgSlot *sc = &ctrl->slot[L % PG_NUM_SLOTS];
-        PgSlot *sn = &ctrl->slot[(L + 1) % PG_NUM_SLOTS];
-        const uint32_t F = __ldcg(&sc->size);
-        const unsigned long long E = pg_ldcg64(&sc->out_edges);
+        MsCount *cc = &A.cnt[L & 3u];
+        MsCount *cn = &A.cnt[(L + 1u) & 3u];
+        const uint32_t F = __ldcg(&cc->F);
+        const unsigned long long E = pg_ldcg64(&cc->E);
         if (F == 0) break;
         if (A.max_rounds && L >= A.max_rounds) {
             if (gtid == 0) atomicOr(&ctrl->status, PG_DEV_OVERFLOW);
             break;
         }
         if (gtid == 0) {
-            PgSlot *sr = &ctrl->slot[(L + 2) % PG_NUM_SLOTS];
-            sr->size = 0;
-            sr->out_edges = 0;
+            MsCount *cr = &A.cnt[(L + 2u) & 3u];  // neither read nor filled in this round
+            cr->F = 0;
+            cr->T = 0;
+            cr->U = 0;
+            cr->E = 0;
             if (pg_gtimer() > t_deadline) atomicOr(&ctrl->status, PG_DEV_TIMEOUT);
         }
         if (A.allow_pull && A.direction == PG_DIR_AUTO) {
@@ -162,25 +240,57 @@ __global__ void __launch_bounds__(512) pg_msbfs_kernel(const MsArgs A) {
             bottom_up = false;
         }
         edges_seen += E;
+        const uint32_t cur = L & 1u;
+        const unsigned long long *visit_cur = cur ? A.visit1 : A.visit0;
+        unsigned long long *visit_nxt = cur ? A.visit0 : A.visit1;
+        const uint32_t *front_cur = cur ? A.front1 : A.front0;
+        uint32_t *front_nxt = cur ? A.front0 : A.front1;
+        const uint32_t dnew = L + 1u;
+        unsigned long long ne = 0;  // out-degree sum of the next frontier
         if (bottom_up) {
             pulls++;
-            // light vertices: one thread each, kGather gathers in flight
-            for (uint32_t w = gtid; w < n; w += gthreads) {
-                const unsigned long long need = full & ~A.seen[w];
-                if (!need) continue;
-                const uint32_t b = __ldg(A.G.toff + w), e = __ldg(A.G.toff + w + 1);
-                if (e - b >= kHeavy) continue;  // in the chunk list
-                unsigned long long acc = 0;
-                for (uint32_t q = b; q < e; q += kGather) {
-                    uint32_t u[kGather];
+            const uint32_t *ulist = up ? A.unfin1 : A.unfin0;
+            uint32_t *unext = up ? A.unfin0 : A.unfin1;
+            const uint32_t U = uall ? n : Ucur;
+            // light vertices: one thread each, kGather gathers in flight;
+            // warps take consecutive list positions (whole-warp appends)
+            for (uint32_t b0 = gwarp * 32u; b0 < U; b0 += nwarps * 32u) {
+                const uint32_t i = b0 + (uint32_t)lane;
+                uint32_t w = PG_NONE;
+                if (i < U) w = uall ? i : __ldcg(ulist + i);
+                unsigned long long s = 0, nb = 0;
+                bool keep = false, light = false;
+                if (w != PG_NONE) {
+                    s = A.seen[w];
+                    const unsigned long long need = full & ~s;
+                    if (need) {
+                        const uint32_t b = __ldg(A.G.toff + w), e = __ldg(A.G.toff + w + 1);
+                        if (e - b < kHeavy) {
+                            light = true;
+                            unsigned long long acc = 0;
+                            for (uint32_t q = b; q < e; q += kGather) {
+                                uint32_t u[kGather];
 #pragma unroll
-                    for (int i = 0; i < (int)kGather; i++) u[i] = (q + i < e) ? __ldg(A.G.tidx + q + i) : PG_NONE;
+                                for (int t = 0; t < (int)kGather; t++)
+                                    u[t] = (q + t < e) ? __ldg(A.G.tidx + q + t) : PG_NONE;
 #pragma unroll
-                    for (int i = 0; i < (int)kGather; i++)
-                        if (u[i] != PG_NONE) acc |= __ldcg(A.visit + u[i]);
-                    if ((acc & need) == need) break;
+                                for (int t = 0; t < (int)kGather; t++)
+                                    if (u[t] != PG_NONE) acc |= __ldcg(visit_cur + u[t]);
+                                if ((acc & need) == need) break;
+                            }
+                            nb = acc & need;
+                            if (nb) {
+                                A.seen[w] = s | nb;
+                                record_bits(A, visit_nxt, w, nb, dnew);
+                                ne += __ldg(A.G.off + w + 1) - __ldg(A.G.off + w);
+                            }
+                            keep = nb != need && e > b;  // still missing bits, reachable
+                        }
+                        // heavy vertices are updated (and listed) by the chunk pass
+                    }
                 }
-                if (acc & need) A.next[w] = acc & need;
+                list_append(front_nxt, &cn->F, light && nb != 0, w, lane);
+                list_append(unext, &cn->U, keep, w, lane);
             }
             // heavy vertices: one warp per chunk of in-edges
             for (uint32_t c = gwarp; c < A.nchunks_in; c += nwarps) {
@@ -191,27 +301,56 @@ __global__ void __launch_bounds__(512) pg_msbfs_kernel(const MsArgs A) {
                 const uint32_t e = min(ch.y + kChunk, __ldg(A.G.toff + w + 1));
                 unsigned long long acc = 0;
                 for (uint32_t q = ch.y; q < e; q += 32u) {
-                    if (q + lane < e) acc |= __ldcg(A.visit + __ldg(A.G.tidx + q + lane));
+                    if (q + lane < e) acc |= __ldcg(visit_cur + __ldg(A.G.tidx + q + lane));
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) acc |= __shfl_xor_sync(kFull, acc, o);
                     if ((acc & need) == need) break;
                 }
                 if (lane == 0 && (acc & need)) atomicOr(A.next + w, acc & need);
             }
+            if (A.nchunks_in) {
+                if (!pg_grid_sync(ctrl, gridDim.x, gen, A.timeout_ns, &s_flag)) break;
+                // update of the heavy vertices (each at its first chunk)
+                for (uint32_t c0 = gwarp * 32u; c0 < A.nchunks_in; c0 += nwarps * 32u) {
+                    const uint32_t c = c0 + (uint32_t)lane;
+                    uint32_t w = PG_NONE;
+                    bool grew = false, keep = false;
+                    if (c < A.nchunks_in) {
+                        const uint2 ch = A.chunks_in[c];
+                        if (ch.y == __ldg(A.G.toff + ch.x)) w = ch.x;
+                    }
+                    if (w != PG_NONE) {
+                        const unsigned long long s = A.seen[w];
+                        if ((s & full) != full) {
+                            const unsigned long long nx = __ldcg(A.next + w);
+                            const unsigned long long nb = nx & ~s & full;
+                            if (nx) A.next[w] = 0;
+                            if (nb) {
+                                A.seen[w] = s | nb;
+                                record_bits(A, visit_nxt, w, nb, dnew);
+                                ne += __ldg(A.G.off + w + 1) - __ldg(A.G.off + w);
+                                grew = true;
+                            }
+                            keep = ((s | nb) & full) != full;
+                        }
+                    }
+                    list_append(front_nxt, &cn->F, grew, w, lane);
+                    list_append(unext, &cn->U, keep, w, lane);
+                }
+            }
         } else {
-            // top-down: warps take 32 consecutive vertices, expand the
-            // active ones' edges cooperatively (32 edges per step)
-            for (uint32_t base = gwarp * 32u; base < n; base += nwarps * 32u) {
-                const uint32_t v = base + lane;
+            // top-down: warps take 32 consecutive frontier entries and expand
+            // their edges cooperatively (32 edges per step)
+            for (uint32_t b0 = gwarp * 32u; b0 < F; b0 += nwarps * 32u) {
+                const uint32_t i = b0 + (uint32_t)lane;
                 unsigned long long bits = 0;
                 uint32_t beg = 0, deg = 0;
-                if (v < n) {
-                    bits = __ldcg(A.visit + v);
-                    if (bits) {
-                        beg = __ldg(A.G.off + v);
-                        deg = __ldg(A.G.off + v + 1) - beg;
-                        if (deg >= kHeavy) deg = 0;  // in the chunk list
-                    }
+                if (i < F) {
+                    const uint32_t v = __ldcg(front_cur + i);
+                    bits = __ldcg(visit_cur + v);
+                    beg = __ldg(A.G.off + v);
+                    deg = __ldg(A.G.off + v + 1) - beg;
+                    if (deg >= kHeavy) deg = 0;  // in the chunk list
                 }
                 uint32_t incl = deg;
 #pragma unroll
@@ -225,71 +364,97 @@ __global__ void __launch_bounds__(512) pg_msbfs_kernel(const MsArgs A) {
                 s_base[wib][lane] = beg - (incl - deg);
                 s_bits[wib][lane] = bits;
                 __syncwarp();
-                for (uint32_t j = lane; j < total; j += 32) {
-                    uint32_t o = 0;
+                for (uint32_t j0 = 0; j0 < total; j0 += 32u) {
+                    const uint32_t j = j0 + (uint32_t)lane;
+                    uint32_t w = 0;
+                    bool first = false;
+                    if (j < total) {
+                        uint32_t o = 0;
 #pragma unroll
-                    for (uint32_t step = 16; step >= 1; step >>= 1)
-                        if (s_incl[wib][o + step - 1] <= j) o += step;
-                    const uint32_t e = s_base[wib][o] + j;  // u32 sum (the base may wrap)
-                    const uint32_t w = __ldg(A.G.idx + e);
-                    atomicOr(A.next + w, s_bits[wib][o]);
+                        for (uint32_t step = 16; step >= 1; step >>= 1)
+                            if (s_incl[wib][o + step - 1] <= j) o += step;
+                        const uint32_t e = s_base[wib][o] + j;  // u32 sum (the base may wrap)
+                        w = __ldg(A.G.idx + e);
+                        first = atomicOr(A.next + w, s_bits[wib][o]) == 0ull;
+                    }
+                    list_append(A.touched, &cn->T, first, w, lane);
                 }
                 __syncwarp();
             }
-            // heavy frontier vertices: one warp per chunk of out-edges
+            // heavy frontier vertices: one warp per chunk of out-edges (only
+            // the vertices that joined this round's frontier)
             for (uint32_t c = gwarp; c < A.nchunks_out; c += nwarps) {
                 const uint2 ch = A.chunks_out[c];
-                const unsigned long long bits = __ldcg(A.visit + ch.x);
+                if (__ldcg(A.flev + ch.x) != L) continue;
+                const unsigned long long bits = __ldcg(visit_cur + ch.x);
                 if (!bits) continue;
                 const uint32_t e = min(ch.y + kChunk, __ldg(A.G.off + ch.x + 1));
-                for (uint32_t q = ch.y + lane; q < e; q += 32u) atomicOr(A.next + __ldg(A.G.idx + q), bits);
-            }
-        }
-        if (!pg_grid_sync(ctrl, gridDim.x, gen, A.timeout_ns, &s_flag)) break;
-        // update: new bits -> distances, next frontier statistics
-        unsigned long long nv = 0, ne = 0;
-        for (uint32_t b0 = gwarp * 32u; b0 < n; b0 += nwarps * 32u) {
-            const uint32_t v = b0 + lane;
-            unsigned long long nb = 0;
-            if (v < n) {
-                const unsigned long long nx = __ldcg(A.next + v);
-                const unsigned long long sn_ = A.seen[v];
-                nb = nx & ~sn_ & full;
-                if (nx) A.next[v] = 0;
-                if (A.visit[v] != nb) A.visit[v] = nb;
-                if (nb) {
-                    A.seen[v] = sn_ | nb;
-                    nv++;
-                    ne += __ldg(A.G.off + v + 1) - __ldg(A.G.off + v);
+                for (uint32_t q0 = ch.y; q0 < e; q0 += 32u) {
+                    const uint32_t q = q0 + (uint32_t)lane;
+                    uint32_t w = 0;
+                    bool first = false;
+                    if (q < e) {
+                        w = __ldg(A.G.idx + q);
+                        first = atomicOr(A.next + w, bits) == 0ull;
+                    }
+                    list_append(A.touched, &cn->T, first, w, lane);
                 }
             }
-            if (__any_sync(kFull, nb != 0)) {
-                for (uint32_t j = 0; j < k; j++)
-                    if ((nb >> j) & 1ull) A.dist[(size_t)j * n + v] = L + 1;
+            if (!pg_grid_sync(ctrl, gridDim.x, gen, A.timeout_ns, &s_flag)) break;
+            // update of the touched vertices
+            const uint32_t T = __ldcg(&cn->T);
+            for (uint32_t b0 = gwarp * 32u; b0 < T; b0 += nwarps * 32u) {
+                const uint32_t i = b0 + (uint32_t)lane;
+                uint32_t w = 0;
+                bool grew = false;
+                if (i < T) {
+                    w = __ldcg(A.touched + i);
+                    const unsigned long long nx = __ldcg(A.next + w);
+                    A.next[w] = 0;
+                    const unsigned long long s = A.seen[w];
+                    const unsigned long long nb = nx & ~s & full;
+                    if (nb) {
+                        A.seen[w] = s | nb;
+                        record_bits(A, visit_nxt, w, nb, dnew);
+                        ne += __ldg(A.G.off + w + 1) - __ldg(A.G.off + w);
+                        grew = true;
+                    }
+                }
+                list_append(front_nxt, &cn->F, grew, w, lane);
             }
         }
-        nv = wsum(nv);
         ne = wsum(ne);
-        if (lane == 0 && nv) {
-            atomicAdd(&sn->size, (unsigned)nv);
-            atomicAdd(&sn->out_edges, ne);
-        }
+        if (lane == 0 && ne) atomicAdd(&cn->E, ne);
         if (!pg_grid_sync(ctrl, gridDim.x, gen, A.timeout_ns, &s_flag)) break;
-    }
-    // sources never reached: 0xFFFFFFFF
-    if (pg_ld_volatile(&ctrl->status) == 0u) {
-        for (uint32_t b0 = gwarp * 32u; b0 < n; b0 += nwarps * 32u) {
-            const uint32_t v = b0 + lane;
-            const unsigned long long miss = (v < n) ? (full & ~A.seen[v]) : 0ull;
-            if (__any_sync(kFull, miss != 0)) {
-                for (uint32_t j = 0; j < k; j++)
-                    if ((miss >> j) & 1ull) A.dist[(size_t)j * n + v] = PG_INF;
-            }
+        if (bottom_up) {
+            Ucur = __ldcg(&cn->U);
+            up ^= 1u;
+            uall = false;
         }
     }
     if (gtid == 0) {
         ctrl->rounds = L;
         ctrl->pull_rounds = pulls;
+    }
+}
+
+// Distances from the planes: dist[j * n + v] for every source j (coalesced
+// over v); 0xFFFFFFFF where bit j never arrived; code 31 was written directly.
+__global__ void k_msbfs_decode(const unsigned long long *seen, const unsigned long long *planes,
+                               uint32_t n, uint32_t k, uint32_t *dist) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const unsigned long long s = seen[v];
+        unsigned long long p[kPlanes];
+#pragma unroll
+        for (uint32_t b = 0; b < kPlanes; b++) p[b] = planes[(size_t)b * n + v];
+        for (uint32_t j = 0; j < k; j++) {
+            uint32_t code = 0;
+#pragma unroll
+            for (uint32_t b = 0; b < kPlanes; b++) code |= (uint32_t)((p[b] >> j) & 1ull) << b;
+            if (!((s >> j) & 1ull)) dist[(size_t)j * n + v] = PG_INF;
+            else if (code != kDirect) dist[(size_t)j * n + v] = code;
+        }
     }
 }
 
@@ -324,33 +489,47 @@ static pg_status build_chunks(pg_graph *g, const uint32_t *off, uint2 **out, uin
 pg_status pg_launch_msbfs(pg_graph *g, PgLaunch &L, const uint32_t *sources, uint32_t k,
                           uint32_t *dist, cudaStream_t s) {
     if (!g->msbfs) {
-        g->msbfs = new PgMsbfsWork();
-        memset(g->msbfs, 0, sizeof(PgMsbfsWork));
+        PgMsbfsWork *W = new PgMsbfsWork();
+        memset(W, 0, sizeof(PgMsbfsWork));
+        const size_t n = g->n;
         unsigned long long *p = nullptr;
-        cudaError_t e = cudaMalloc(&p, (size_t)3 * g->n * sizeof(unsigned long long));
+        uint32_t *q = nullptr;
+        cudaError_t e = cudaMalloc(&p, (4 + kPlanes) * n * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMalloc(&q, 6 * n * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&W->cnt, 4 * sizeof(MsCount));
         if (e != cudaSuccess) {
-            delete g->msbfs;
-            g->msbfs = nullptr;
+            cudaFree(p);
+            cudaFree(q);
+            delete W;
             return pg_cuda_error(e, "cudaMalloc(batched BFS words)");
         }
-        g->msbfs->seen = p;
-        g->msbfs->visit = p + g->n;
-        g->msbfs->next = p + 2 * (size_t)g->n;
-        g->msbfs->n = g->n;
+        W->seen = p;
+        W->visit[0] = p + n;
+        W->visit[1] = p + 2 * n;
+        W->next = p + 3 * n;
+        W->planes = p + 4 * n;
+        W->front[0] = q;
+        W->front[1] = q + n;
+        W->unfin[0] = q + 2 * n;
+        W->unfin[1] = q + 3 * n;
+        W->touched = q + 4 * n;
+        W->flev = q + 5 * n;
+        W->n = g->n;
+        g->msbfs = W;
         const bool self = g->transpose_is_self || !g->d_toff;
         for (int d = 0; d < (self ? 1 : 2); d++) {
-            pg_status st = build_chunks(g, d ? g->d_toff : g->d_off, &g->msbfs->chunks[d],
-                                        &g->msbfs->nchunks[d], s);
+            pg_status st = build_chunks(g, d ? g->d_toff : g->d_off, &W->chunks[d], &W->nchunks[d], s);
             if (st) {
                 pg_msbfs_release(g);
                 return st;
             }
         }
         if (self) {
-            g->msbfs->chunks[1] = g->msbfs->chunks[0];
-            g->msbfs->nchunks[1] = g->msbfs->nchunks[0];
+            W->chunks[1] = W->chunks[0];
+            W->nchunks[1] = W->nchunks[0];
         }
     }
+    PgMsbfsWork &W = *g->msbfs;
     MsArgs A;
     memset(&A, 0, sizeof(A));
     A.G.off = g->d_off;
@@ -359,14 +538,23 @@ pg_status pg_launch_msbfs(pg_graph *g, PgLaunch &L, const uint32_t *sources, uin
     A.G.tidx = g->d_tidx ? g->d_tidx : g->d_idx;
     A.G.n = g->n;
     A.G.m = g->m;
-    A.chunks_out = g->msbfs->chunks[0];
-    A.nchunks_out = g->msbfs->nchunks[0];
-    A.chunks_in = g->msbfs->chunks[1];
-    A.nchunks_in = g->has_transpose ? g->msbfs->nchunks[1] : 0u;
+    A.chunks_out = W.chunks[0];
+    A.nchunks_out = W.nchunks[0];
+    A.chunks_in = W.chunks[1];
+    A.nchunks_in = g->has_transpose ? W.nchunks[1] : 0u;
     A.ctrl = g->d_ctrl;
-    A.seen = g->msbfs->seen;
-    A.visit = g->msbfs->visit;
-    A.next = g->msbfs->next;
+    A.cnt = W.cnt;
+    A.seen = W.seen;
+    A.visit0 = W.visit[0];
+    A.visit1 = W.visit[1];
+    A.next = W.next;
+    A.planes = W.planes;
+    A.front0 = W.front[0];
+    A.front1 = W.front[1];
+    A.unfin0 = W.unfin[0];
+    A.unfin1 = W.unfin[1];
+    A.touched = W.touched;
+    A.flev = W.flev;
     A.dist = dist;
     A.k = k;
     for (uint32_t j = 0; j < k; j++) A.sources[j] = sources[j];
@@ -385,10 +573,13 @@ pg_status pg_launch_msbfs(pg_graph *g, PgLaunch &L, const uint32_t *sources, uin
     L.blocks = bps;
     L.threads = threads;
     PG_CK(cudaMemsetAsync(g->d_ctrl, 0, sizeof(PgCtrl), s));
+    PG_CK(cudaMemsetAsync(W.cnt, 0, 4 * sizeof(MsCount), s));
     void *args[] = {(void *)&A};
     PG_CK(cudaEventRecord(g->ev0, s));
     PG_CK(cudaLaunchCooperativeKernel((const void *)pg_msbfs_kernel, dim3(bps * g->num_sms),
                                       dim3(threads), args, 0, s));
+    k_msbfs_decode<<<g->num_sms * 8, 256, 0, s>>>(W.seen, W.planes, g->n, k, dist);
+    PG_CK(cudaGetLastError());
     PG_CK(cudaEventRecord(g->ev1, s));
     return PG_OK;
 }

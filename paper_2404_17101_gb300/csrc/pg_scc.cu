@@ -106,6 +106,7 @@ struct SccArgs {
     PgCtrl *ctrl;
     uint32_t tau, qcap;
     unsigned long long timeout_ns;
+    uint32_t stall_block;             // fault injection: this CTA never arrives at the grid barrier
 };
 
 struct SccWarp {
@@ -237,6 +238,7 @@ __global__ void __launch_bounds__(512, 1) k_scc_search(const SccArgs A) {
         if (v < n && __ldg(A.part + v) != PG_NONE) seed = kColor ? true : (A.flag[v] == 1u);
         scc_push(A, &ctrl->slot[0], 0u, 0u, seed, false, v, lane);
     }
+    if (A.stall_block == blockIdx.x) return;  // fault injection: never arrive
     if (!pg_grid_sync(ctrl, gridDim.x, gen, A.timeout_ns, &s_flag)) return;
 
     const unsigned long long t_deadline = pg_gtimer() + 16ull * A.timeout_ns;
@@ -449,6 +451,7 @@ extern "C" pg_status pg_scc(pg_graph *g, uint32_t *label_out, const pg_config *c
     A.tau = tau;
     A.qcap = qcap;
     A.timeout_ns = timeout_ns;
+    A.stall_block = c->test_stall_block;
 
     PG_CK(cudaEventRecord(g->ev0, s));
     k_scc_init<<<grid, 256, 0, s>>>(n, W.part, W.rep);

@@ -97,9 +97,22 @@ struct WarpSm {
     unsigned long long *s_val;                  // [32]
 };
 
+// Per-CTA aggregates of one round, in shared memory: warps add to them with
+// shared-memory atomics, and thread 0 adds them to the global counters once
+// per round inside the round barrier (pg_grid_sync_then), so the global
+// counters see one atomic per CTA instead of one per warp.
+struct CtaStat {
+    unsigned long long exp_edges;  // edges expanded in the round
+    unsigned long long out_edges;  // out-degree sum of the entries appended to the next bag
+    unsigned exp_verts;            // vertices expanded in the round
+    unsigned min_level, max_level; // BFS: distance range of attempted appends
+    unsigned pad;
+};
+
 struct Round {
     uint32_t cur, nxt;       // storage parity
     PgSlot *sc, *sn;         // counters of the bag read / filled
+    CtaStat *cs;             // this CTA's aggregates of the round
     uint32_t tag;            // round tag of the bag being filled
     uint32_t tau;
     uint32_t F;
@@ -133,6 +146,7 @@ struct CtaSm {
     uint32_t *ent[3], *aux[3];  // three level buffers, rotating
     unsigned *n;                // [3] level sizes
     unsigned *task;             // grabbed task base
+    unsigned *wcnt;             // [warps + 1] spill counts / offsets of a CTA flush
 };
 
 struct Counters {
@@ -180,14 +194,17 @@ __device__ __forceinline__ const uint32_t *row_idx(const TravArgs &A, uint32_t d
 // collective: every lane calls it with the same control flow.
 //   - de-duplication: atomicExch of the round tag into stamp[key] (skipped
 //     when the round cannot produce duplicates)
-//   - one atomicAdd on the bag tail per call
+//   - one atomicAdd on the bag tail per call; with kCta, the call is
+//     CTA-collective (every thread of the CTA makes it, wcnt = [warps + 1]
+//     shared words) and thread 0 makes one reservation for all warps, so the
+//     bag tail sees one atomic per CTA instead of one per warp
 //   - out-degree sum (schedule statistics) and hub registration when needed
 //   - BFS: min / max distance over all attempted appends (kept even when the
 //     append was de-duplicated); the min defines the settled level.
-template <bool kReach>
+template <bool kReach, bool kCta = false>
 __device__ void push_global(const TravArgs &A, const Round &R, const uint32_t (&ent)[kU],
                             const uint32_t (&nd)[kU], const bool (&go)[kU], int lane,
-                            Counters &C) {
+                            Counters &C, unsigned *wcnt = nullptr) {
     bool keep[kU];
     uint32_t deg[kU], prev[kU];
     const bool want_deg = A.need_deg || A.hubs_possible;
@@ -231,14 +248,32 @@ __device__ void push_global(const TravArgs &A, const Round &R, const uint32_t (&
         mn = warp_min(mn);
         mx = warp_max(mx);
         if (lane == 0 && mn != PG_INF) {
-            atomicMin(&R.sn->min_level, mn);
-            atomicMax(&R.sn->max_level, mx);
+            atomicMin(&R.cs->min_level, mn);
+            atomicMax(&R.cs->max_level, mx);
         }
     }
-    if (total == 0) return;
     uint32_t pos = 0;
-    if (lane == 0) pos = atomicAdd(&R.sn->size, total);
-    pos = __shfl_sync(kFull, pos, 0);
+    if (kCta) {
+        const int wib = threadIdx.x >> 5, nwib = blockDim.x >> 5;
+        if (lane == 0) wcnt[wib] = total;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t sum = 0;
+            for (int w = 0; w < nwib; w++) {
+                const uint32_t c = wcnt[w];
+                wcnt[w] = sum;
+                sum += c;
+            }
+            wcnt[nwib] = sum ? atomicAdd(&R.sn->size, sum) : 0u;
+        }
+        __syncthreads();
+        pos = wcnt[nwib] + wcnt[wib];
+        if (total == 0) return;
+    } else {
+        if (total == 0) return;
+        if (lane == 0) pos = atomicAdd(&R.sn->size, total);
+        pos = __shfl_sync(kFull, pos, 0);
+    }
     const unsigned lt = pg_lanemask_lt();
     unsigned long long dsum = 0;
 #pragma unroll
@@ -268,7 +303,7 @@ __device__ void push_global(const TravArgs &A, const Round &R, const uint32_t (&
     }
     if (want_deg) {
         dsum = warp_sum64(dsum);
-        if (lane == 0 && dsum) atomicAdd(&R.sn->out_edges, dsum);
+        if (lane == 0 && dsum) atomicAdd(&R.cs->out_edges, dsum);
     }
     C.pushes += (lane == 0) ? total : 0;
 }
@@ -290,6 +325,27 @@ __device__ void flush_spill(const TravArgs &A, const Round &R, const WarpSm &S, 
         }
         push_global<kReach>(A, R, ent, nd, go, lane, C);
     }
+    T.nsp = 0;
+    __syncwarp();
+}
+
+// End-of-task flush of the CTA local search: every warp's staged spills (at
+// most kSpillCap each, one batch) with one bag reservation for the CTA.
+// CTA-collective.
+template <bool kReach>
+__device__ void flush_spill_cta(const TravArgs &A, const Round &R, const WarpSm &S, Task &T,
+                                unsigned *wcnt, int lane, Counters &C) {
+    __syncwarp();
+    uint32_t ent[kU], nd[kU];
+    bool go[kU];
+#pragma unroll
+    for (int u = 0; u < kU; u++) {
+        const uint32_t i = (uint32_t)u * 32u + (uint32_t)lane;
+        go[u] = i < T.nsp;
+        ent[u] = go[u] ? S.sp[i] : 0u;
+        nd[u] = go[u] ? S.spa[i] : 0u;
+    }
+    push_global<kReach, true>(A, R, ent, nd, go, lane, C, wcnt);
     T.nsp = 0;
     __syncwarp();
 }
@@ -636,6 +692,92 @@ __device__ void expand_rows_sp(const TravArgs &A, const Round &R, const WarpSm &
     }
 }
 
+// One level of the CTA's BFS local search over forward padded rows of width
+// W = 2^LW, in its shortest instruction path (the level's latency is the
+// warps' instruction paths plus one row read and one atomicMin round trip).
+// Lane l of a wave takes entry w0 + l / W and slot l % W of its row: it
+// relaxes at most one arc, and the children inside the
+// window are appended to the CTA's next level with one shared-memory atomic
+// per warp; the others go to the warp's spill staging.  Entries whose list
+// is in the CSR (every slot marked PG_ELL_LONG) are expanded afterwards, one
+// per lane, by the generic expand_wave.
+template <uint32_t LW>
+__device__ void bfs_rows_level(const TravArgs &A, const Round &R, const WarpSm &S, Task &T,
+                               const uint32_t *ents, const uint32_t *auxs, uint32_t ncur,
+                               bool from_bag, int lane, int wib, int nwib, Counters &C) {
+    constexpr uint32_t W = 1u << LW, G = 32u >> LW;
+    const uint32_t j = (uint32_t)lane & (W - 1u);
+    const uint32_t win = R.Lbase + R.tau;  // children at distance < win stay in the CTA
+    const unsigned lt = pg_lanemask_lt();
+    const uint32_t *ell = A.ell0;
+    for (uint32_t w0 = (uint32_t)wib * G; w0 < ncur; w0 += (uint32_t)nwib * G) {
+        const uint32_t i = w0 + ((uint32_t)lane >> LW);
+        uint32_t v = PG_NONE, aux = 0, nd = PG_INF;
+        if (i < ncur) {
+            v = PG_DBG_ENTRY(A, ents[i], 10u, false);
+            aux = auxs[i];
+        }
+        if (v != PG_NONE) {
+            // a local-search entry carries its distance; a bag entry reads it
+            const uint32_t d = from_bag ? pg_ldcg(A.dist + v) : aux;
+            nd = (d == PG_INF) ? PG_INF : d + 1u;
+        }
+        const bool live = nd != PG_INF;
+        uint32_t x = PG_NONE;
+        if (live) x = __ldg(ell + (size_t)v * W + j);
+#ifdef PG_DEBUG_BOUNDS
+        if (x < 0x80000000u) x = PG_DBG_ID(A, x, 11u, false);
+#endif
+        const bool arc = x < 0x80000000u;  // not padding, not a CSR-row marker
+        const bool loc = nd < win;
+        uint32_t old = 0;
+        if (arc) old = atomicMin(A.dist + x, nd);
+        if (arc && loc) pg_prefetch_l1(ell + (size_t)x * W);
+        const bool imp = arc && nd < old;
+        const bool is_long = live && j == 0u && x == PG_ELL_LONG;
+        if (live && j == 0u && !is_long) { C.expansions++; C.exp_verts++; }
+        if (arc) C.exp_edges++;
+        // children inside the window: the CTA's next level
+        bool spill = imp && !loc;
+        const unsigned bl = __ballot_sync(kFull, imp && loc);
+        if (bl) {
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(T.cta_n, (unsigned)__popc(bl));
+            base = __shfl_sync(kFull, base, 0);
+            const uint32_t p = base + __popc(bl & lt);
+            if (imp && loc) {
+                if (p < T.cta_cap) {
+                    T.cta_ent[p] = x;
+                    T.cta_aux[p] = nd;
+                } else {
+                    spill = true;  // the level buffer is full
+                }
+            }
+        }
+        // children beyond the window (or overflow): the warp's spill staging
+        const unsigned bs = __ballot_sync(kFull, spill);
+        if (bs) {
+            if (T.nsp + (uint32_t)__popc(bs) > kSpillCap) flush_spill<false>(A, R, S, T, lane, C);
+            if (spill) {
+                const uint32_t p = T.nsp + __popc(bs & lt);
+                S.sp[p] = x;
+                S.spa[p] = nd;
+            }
+            T.nsp += __popc(bs);
+        }
+        // lists kept in the CSR: lane t takes the t-th such entry
+        const unsigned bll = __ballot_sync(kFull, is_long);
+        if (bll) {
+            unsigned mm = bll;
+            for (int q = 0; q < lane && mm; q++) mm &= mm - 1u;
+            const int src = mm ? __ffs(mm) - 1 : 0;
+            const uint32_t e2 = __shfl_sync(kFull, v, src);
+            const uint32_t a2 = __shfl_sync(kFull, aux, src);
+            expand_wave<false>(A, R, S, T, mm ? e2 : PG_NONE, a2, from_bag, lane, C);
+        }
+    }
+}
+
 // One warp task: c frontier entries plus the local search they start.
 template <bool kReach>
 __device__ void run_task(const TravArgs &A, const Round &R, const WarpSm &S, uint32_t entry,
@@ -706,7 +848,15 @@ __device__ void cta_round(const TravArgs &A, const Round &R, const WarpSm &S, co
             T.cta_aux = Q.aux[nl];
             T.cta_n = &Q.n[nl];
             T.cta_cap = QC;
-            if (lw) {
+            if (!kReach && A.ellw0 != 0u) {
+                // BFS reads the forward rows only: the lean level of width ellw0
+                if (A.ellw0 == 4u)
+                    bfs_rows_level<2>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C);
+                else if (A.ellw0 == 8u)
+                    bfs_rows_level<3>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C);
+                else
+                    bfs_rows_level<4>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C);
+            } else if (lw) {
                 const uint32_t G = 32u >> lw;  // entries per slot-parallel wave
                 for (uint32_t w0 = (uint32_t)wib * G; w0 < ncur; w0 += (uint32_t)nwib * G)
                     expand_rows_sp<kReach>(A, R, S, T, Q.ent[cl], Q.aux[cl], w0, ncur, lw, h == 0, lane, C);
@@ -722,7 +872,7 @@ __device__ void cta_round(const TravArgs &A, const Round &R, const WarpSm &S, co
             __syncthreads();
         }
         T.cta_n = nullptr;
-        flush_spill<kReach>(A, R, S, T, lane, C);
+        flush_spill_cta<kReach>(A, R, S, T, Q.wcnt, lane, C);
         if (R.F <= span) break;
         if (threadIdx.x == 0) *Q.task = span + atomicAdd(&R.sc->head, cc);
         __syncthreads();
@@ -942,6 +1092,12 @@ __device__ __forceinline__ float flog2p1(float x) { return log2f(1.0f + x); }
 // not evaluated outside that range.
 constexpr uint32_t kRoundFeatureCap = 1u << 14;
 
+// Per-warp FIFO words (entry + aux per slot): only the warp local search
+// uses the FIFO, so the CTA local search leaves it out of shared memory.
+__host__ __device__ __forceinline__ uint32_t warp_fifo_words(const PgLaunch &L) {
+    return L.vgc == PG_VGC_CTA ? 0u : L.qcap;
+}
+
 template <bool kReach>
 __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -956,10 +1112,11 @@ __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
 
     // shared memory: MLP weights, then per warp: s_val[32] (u64), 4 x [32]
     // u32 wave arrays, spill staging 2 x [kSpillCap], local FIFO 2 x [qcap]
+    // (the per-warp FIFO is used by the warp local search only)
     float *s_w = reinterpret_cast<float *>(smem);
     unsigned long long *s_val_all = reinterpret_cast<unsigned long long *>(smem + 6144);
     uint32_t *s_u32 = reinterpret_cast<uint32_t *>(smem + 6144 + nwib * 256);
-    const uint32_t per_warp = 4u * 32u + 2u * kSpillCap + 2u * A.L.qcap;
+    const uint32_t per_warp = 4u * 32u + 2u * kSpillCap + 2u * warp_fifo_words(A.L);
     uint32_t *mine = s_u32 + (size_t)wib * per_warp;
     WarpSm S;
     S.s_val = s_val_all + wib * 32;
@@ -980,6 +1137,16 @@ __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
         }
         Q.n = cta + 6u * A.L.cta_queue;
         Q.task = Q.n + 3;
+    }
+    __shared__ unsigned s_wcnt[17];
+    Q.wcnt = s_wcnt;
+    __shared__ CtaStat s_cs;
+    if (threadIdx.x == 0) {
+        s_cs.exp_edges = 0;
+        s_cs.out_edges = 0;
+        s_cs.exp_verts = 0;
+        s_cs.min_level = PG_INF;
+        s_cs.max_level = 0;
     }
 
     if (A.L.schedule == PG_SCHED_LEARNED)
@@ -1060,18 +1227,34 @@ __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
     uint32_t pull_rounds = 0;
     uint32_t r = 0;
     unsigned long long t_round = 0;
+    // the round's control words, read once per CTA (thread 0) and shared
+    __shared__ unsigned long long s_in[5];
+    __shared__ uint32_t s_in32[4];
     for (;; r++) {
         Round R;
         R.cur = r & 1u;
         R.nxt = R.cur ^ 1u;
         R.sc = &ctrl->slot[r % PG_NUM_SLOTS];
         R.sn = &ctrl->slot[(r + 1) % PG_NUM_SLOTS];
+        R.cs = &s_cs;
         R.tag = A.L.epoch + r + 1u;
-        R.F = __ldcg(&R.sc->size);
-        const unsigned long long E_exact = pg_ldcg64(&R.sc->out_edges);
-        const uint32_t Lvl = __ldcg(&R.sc->min_level);
-        const uint32_t Lmax = __ldcg(&R.sc->max_level);
-        R.hub_pack = pg_ldcg64(&R.sc->hub_pack);
+        if (threadIdx.x == 0) {
+            s_in32[0] = __ldcg(&R.sc->size);
+            s_in32[1] = __ldcg(&R.sc->min_level);
+            s_in32[2] = __ldcg(&R.sc->max_level);
+            s_in[0] = pg_ldcg64(&R.sc->out_edges);
+            s_in[1] = pg_ldcg64(&R.sc->hub_pack);
+            s_in32[3] = (r > 0) ? __ldcg(&ctrl->exp_verts[(r - 1) & 3]) : 0u;
+            s_in[2] = (r > 0) ? pg_ldcg64(&ctrl->exp_edges[(r - 1) & 3]) : 0ull;
+            s_in[3] = (r >= 2) ? pg_ldcg64(&ctrl->round_t[(r - 1) & 3]) : 0ull;
+            s_in[4] = (r >= 2) ? pg_ldcg64(&ctrl->round_t[(r - 2) & 3]) : 0ull;
+        }
+        __syncthreads();
+        R.F = s_in32[0];
+        const unsigned long long E_exact = s_in[0];
+        const uint32_t Lvl = s_in32[1];
+        const uint32_t Lmax = s_in32[2];
+        R.hub_pack = s_in[1];
         R.Lbase = Lvl;
         if (R.F == 0) break;
         if ((A.L.max_rounds && r >= A.L.max_rounds) || R.tag == 0u || R.F > A.cap) {
@@ -1082,15 +1265,13 @@ __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
         // mean degree of the vertices expanded in the previous round
         unsigned long long E = E_exact;
         if (!A.need_deg && r > 0) {
-            const unsigned ev = __ldcg(&ctrl->exp_verts[(r - 1) & 3]);
-            const unsigned long long ee = pg_ldcg64(&ctrl->exp_edges[(r - 1) & 3]);
+            const unsigned ev = s_in32[3];
+            const unsigned long long ee = s_in[2];
             const float md = ev ? (float)ee / (float)ev : avg_deg;
             E = (unsigned long long)((float)R.F * md + 0.5f);
         }
         // previous-round time as published by CTA 0 (visible one round late)
-        unsigned long long prev_ns = 0;
-        if (r >= 2)
-            prev_ns = pg_ldcg64(&ctrl->round_t[(r - 1) & 3]) - pg_ldcg64(&ctrl->round_t[(r - 2) & 3]);
+        const unsigned long long prev_ns = (r >= 2) ? s_in[3] - s_in[4] : 0ull;
         float x[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
         if (A.L.schedule == PG_SCHED_LEARNED || A.L.trace != nullptr) {
             x[0] = flog2p1((float)R.F) / 24.f;
@@ -1190,13 +1371,32 @@ __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
             const unsigned long long ee = warp_sum64(C.exp_edges);
             const unsigned long long ev = warp_sum64((unsigned long long)C.exp_verts);
             if (lane == 0 && ev) {
-                atomicAdd(&ctrl->exp_edges[r & 3], ee);
-                atomicAdd(&ctrl->exp_verts[r & 3], (unsigned)ev);
+                atomicAdd(&s_cs.exp_edges, ee);
+                atomicAdd(&s_cs.exp_verts, (unsigned)ev);
             }
             C.exp_edges = 0;
             C.exp_verts = 0;
         }
-        if (!pg_grid_sync(ctrl, nblocks, gen, tmo, &s_flag)) break;
+        // the CTA's aggregates reach the global counters before its arrival
+        PgSlot *sn = R.sn;
+        const uint32_t rr = r & 3;
+        const bool ok = pg_grid_sync_then(ctrl, nblocks, gen, tmo, &s_flag, [&] {
+            if (s_cs.exp_verts) {
+                atomicAdd(&ctrl->exp_edges[rr], s_cs.exp_edges);
+                atomicAdd(&ctrl->exp_verts[rr], s_cs.exp_verts);
+            }
+            if (s_cs.out_edges) atomicAdd(&sn->out_edges, s_cs.out_edges);
+            if (s_cs.min_level != PG_INF) {
+                atomicMin(&sn->min_level, s_cs.min_level);
+                atomicMax(&sn->max_level, s_cs.max_level);
+            }
+            s_cs.exp_edges = 0;
+            s_cs.out_edges = 0;
+            s_cs.exp_verts = 0;
+            s_cs.min_level = PG_INF;
+            s_cs.max_level = 0;
+        });
+        if (!ok) break;
         const unsigned long long t_end = pg_gtimer();
 
         // ---- training traces: vertices already at their final distance
@@ -1239,16 +1439,17 @@ __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
     }
 }
 
-size_t traverse_smem(uint32_t threads, uint32_t qcap, uint32_t cta_queue) {
-    const uint32_t nw = threads / 32;
-    return 6144 + (size_t)nw * 256 + (size_t)nw * (4u * 32u + 2u * kSpillCap + 2u * qcap) * 4u +
-           (size_t)(6u * cta_queue + 4u) * 4u;
+size_t traverse_smem(const PgLaunch &L) {
+    const uint32_t nw = L.threads / 32;
+    return 6144 + (size_t)nw * 256 +
+           (size_t)nw * (4u * 32u + 2u * kSpillCap + 2u * warp_fifo_words(L)) * 4u +
+           (size_t)(6u * L.cta_queue + 4u) * 4u;
 }
 
 template <bool kReach>
 pg_status launch_impl(pg_graph *g, PgLaunch &L, TravArgs &A, cudaStream_t s) {
     auto kern = pg_traverse_kernel<kReach>;
-    const size_t smem = traverse_smem(L.threads, L.qcap, L.cta_queue);
+    const size_t smem = traverse_smem(L);
     int maxopt = 0;
     PG_CK(cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device));
     if (smem > (size_t)maxopt)
@@ -1297,7 +1498,7 @@ pg_status pg_launch_bfs_raw(const PgRawBfs &w, PgLaunch &L, cudaStream_t s) {
     A.need_deg = 0;
     A.hubs_possible = 0;
     auto kern = pg_traverse_kernel<false>;
-    const size_t smem = traverse_smem(L.threads, L.qcap, L.cta_queue);
+    const size_t smem = traverse_smem(L);
     int maxopt = 0;
     PG_CK(cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, w.device));
     if (smem > (size_t)maxopt)

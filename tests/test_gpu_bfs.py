@@ -233,3 +233,18 @@ def test_upload_free_cycles_reuse_pool_memory(pg):
             G.bfs_host(1, h)
             assert np.array_equal(h, w), (cycle, g.name)
             G.free()
+
+
+def test_batched_bfs_barrier_timeout_is_reported_and_recoverable(pg):
+    """pg_bfs_multi's persistent kernel with one CTA that never arrives at the
+    grid barrier (a host-chosen stall): the others give up after timeout_ms,
+    the call returns PG_ERR_TIMEOUT and the next call in the same context is
+    exact."""
+    g = gg.dgrid(40, 40, 5)
+    G = pg.Graph.from_graphgen(g)
+    srcs = gg.pick_sources(g, 8, 2)
+    with pytest.raises(pg.PgError) as e:
+        G.bfs_multi(srcs, cfg=pg.default_config(test_stall_block=1, timeout_ms=300))
+    assert e.value.status == pg.PG_ERR_TIMEOUT
+    D = pg.to_uint32(G.bfs_multi(srcs))
+    assert np.array_equal(D, oracle.bfs_multi(g, srcs))

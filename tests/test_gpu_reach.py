@@ -153,3 +153,21 @@ def test_padded_rows_of_different_widths(pg):
     for s_ in srcs[:4]:
         d = pg.to_uint32(G.bfs(int(s_), cfg=pg.default_config(tau=16)))
         assert np.array_equal(d, oracle.bfs(g, int(s_)))
+
+
+@pytest.mark.parametrize("alpha,beta", [(2, 2), (1000, 2), (1, 1000), (3, 50)])
+@pytest.mark.parametrize("make", [lambda: gg.rmat(16, 16, 21), lambda: gg.knn(60_000, 5, 22),
+                                  lambda: _heavy_directed()])
+def test_bfs_multi_direction_switching(pg, make, alpha, beta):
+    """Batched BFS with push/pull thresholds that switch direction often:
+    top-down rounds that follow bottom-up rounds see visit words left over
+    from older rounds (hubs included), and bottom-up rounds that follow
+    top-down rounds resume from the unfinished list; every row must equal the
+    oracle's BFS."""
+    g = make()
+    G = pg.Graph.from_graphgen(g)
+    srcs = gg.pick_sources(g, 64, 9)
+    st = pg.Stats()
+    D = pg.to_uint32(G.bfs_multi(srcs, cfg=pg.default_config(direction=pg.PG_DIR_AUTO, alpha=alpha,
+                                                              beta=beta), stats=st))
+    assert np.array_equal(D, oracle.bfs_multi(g, srcs)), (st.rounds, st.pull_rounds)

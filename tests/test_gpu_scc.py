@@ -81,3 +81,16 @@ def test_host_output_and_missing_transpose(pg):
     with pytest.raises(pg.PgError) as e:
         H.scc()
     assert e.value.status == pg.PG_ERR_UNSUPPORTED
+
+
+def test_scc_barrier_timeout_is_reported_and_recoverable(pg):
+    """The SCC search kernel with one CTA that never arrives at the grid
+    barrier (a host-chosen stall): PG_ERR_TIMEOUT after timeout_ms, then an
+    exact SCC in the same context."""
+    g = gg.dgrid(40, 40, 5)
+    G = pg.Graph.from_graphgen(g)
+    with pytest.raises(pg.PgError) as e:
+        G.scc(cfg=pg.default_config(test_stall_block=1, timeout_ms=300))
+    assert e.value.status == pg.PG_ERR_TIMEOUT
+    lab, _ = G.scc()
+    assert np.array_equal(pg.to_uint32(lab), oracle.scc(g))
