@@ -465,6 +465,7 @@ static void release(pg_graph *g) {
     if (g->ev1) cudaEventDestroy(g->ev1);
     pg_msbfs_release(g);
     pg_scc_release(g);
+    pg_sssp_release(g);
     delete g;
 }
 
