@@ -64,9 +64,16 @@ typedef enum pg_status {
  *   local search of up to tau levels in shared memory, all its warps
  *   splitting each level (levels separated by a CTA barrier);
  * PG_VGC_WARP: every warp runs its own FIFO local search from a chunk of
- *   `chunk` frontier entries. */
+ *   `chunk` frontier entries;
+ * PG_VGC_BUCKETS: PG_VGC_CTA with the paper's multiple frontiers (Sec. 2.2,
+ *   BFS): the CTA's vertices at depth 2^i form frontier i, and a round's
+ *   local search runs in phases at depths 1, 2, 4, ... < tau separated by
+ *   grid barriers, so no CTA expands frontier i before every CTA has
+ *   finished the nearer ones (fewer vertices expanded before their distance
+ *   is final, at the price of log2(tau) barriers per round). */
 #define PG_VGC_CTA 0u
 #define PG_VGC_WARP 1u
+#define PG_VGC_BUCKETS 2u
 
 /* direction policy for PG_SCHED_FIXED */
 #define PG_DIR_PUSH 0u
@@ -122,7 +129,7 @@ typedef struct pg_config {
     uint32_t script_len;        /* entries in script */
     uint32_t trace_cap;         /* records available in trace_out */
     uint32_t test_stall_block;  /* fault injection: this CTA never arrives at the grid barrier; 0xFFFFFFFF = off */
-    uint32_t vgc_mode;          /* local search for tau > 1: PG_VGC_CTA (default) or PG_VGC_WARP */
+    uint32_t vgc_mode;          /* local search for tau > 1: PG_VGC_CTA (default), PG_VGC_WARP or PG_VGC_BUCKETS */
     uint32_t cta_queue;         /* PG_VGC_CTA: vertices per level a CTA keeps locally (64..8192); 0 = 2048 */
     uint32_t delta;             /* pg_sssp: step width of a round's distance threshold; 0 = 8 x mean weight */
     const uint8_t *script;      /* host: action per round for PG_SCHED_SCRIPT (round i uses script[i % len]) */

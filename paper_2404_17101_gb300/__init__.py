@@ -28,7 +28,7 @@ PG_DIRECTED, PG_BUILD_TRANSPOSE, PG_SKIP_VALIDATE, PG_ELL = 1, 2, 4, 8
 PG_FWD, PG_BWD = 1, 2
 PG_SCHED_FIXED, PG_SCHED_LEARNED, PG_SCHED_RANDOM, PG_SCHED_SCRIPT = 0, 1, 2, 3
 PG_DIR_PUSH, PG_DIR_AUTO = 0, 1
-PG_VGC_CTA, PG_VGC_WARP = 0, 1
+PG_VGC_CTA, PG_VGC_WARP, PG_VGC_BUCKETS = 0, 1, 2
 PG_NUM_ACTIONS, PG_ACTION_PULL = 8, 7
 PG_MLP_NPARAMS = 1512
 INF = 0xFFFFFFFF

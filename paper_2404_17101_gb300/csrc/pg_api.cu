@@ -166,7 +166,7 @@ pg_status pg_resolve_config(pg_graph *g, const pg_config *cfg, PgLaunch *L, cuda
     }
     L->timeout_ns = (unsigned long long)(c->timeout_ms ? c->timeout_ms : 5000) * 1000000ull;
     L->vgc = c->vgc_mode;
-    if (L->vgc > PG_VGC_WARP) return pg_set_error(PG_ERR_INVALID_ARG, "vgc_mode %u", c->vgc_mode);
+    if (L->vgc > PG_VGC_BUCKETS) return pg_set_error(PG_ERR_INVALID_ARG, "vgc_mode %u", c->vgc_mode);
     L->cta_queue = c->cta_queue ? c->cta_queue : 2048;
     if (L->cta_queue < 64 || L->cta_queue > 8192)
         return pg_set_error(PG_ERR_INVALID_ARG, "cta_queue %u not in 64..8192", L->cta_queue);

@@ -809,9 +809,21 @@ __device__ void run_task(const TravArgs &A, const Round &R, const WarpSm &S, uin
 // the window go to the CTA's next-level buffer in shared memory, the rest
 // (and any overflow) spill to the next bag.  Levels are separated by a CTA
 // barrier, so the CTA's local search is itself breadth-first.
+//
+// Multiple frontiers (PG_VGC_BUCKETS; Sec. 2.2, the BFS paragraph): the
+// CTA's level buffer at depth 2^i is its frontier i, the vertices 2^i hops
+// from the round's frontier.  The round's local search is cut into phases
+// at depths 1, 2, 4, ... < tau with a grid barrier between phases, so no
+// frontier i is expanded before every CTA has finished the frontiers
+// nearer than it: a CTA can run ahead of the slowest one by at most the
+// current phase's width, which limits the vertices expanded with a distance
+// that another CTA then shortens ("unready" vertices).  Every CTA takes at
+// most one share (rounds with more entries than the CTAs' level buffers run
+// unphased) and passes every phase barrier, with or without entries.
+// Returns false when a barrier gave up (timeout).
 template <bool kReach>
-__device__ void cta_round(const TravArgs &A, const Round &R, const WarpSm &S, const CtaSm &Q,
-                          int lane, int wib, int nwib, Counters &C) {
+__device__ bool cta_round(const TravArgs &A, const Round &R, const WarpSm &S, const CtaSm &Q,
+                          int lane, int wib, int nwib, Counters &C, unsigned &gen, int *s_flag) {
     const uint32_t nb = gridDim.x;
     const uint32_t QC = A.L.cta_queue;
     // slot-parallel waves when padded rows exist: log2 of the widest row
@@ -820,11 +832,13 @@ __device__ void cta_round(const TravArgs &A, const Round &R, const WarpSm &S, co
     uint32_t cc = (R.F + nb - 1) / nb;
     cc = max(1u, min(cc, QC / 2));
     const uint32_t span = nb * cc;
+    const bool phased = A.L.vgc == PG_VGC_BUCKETS && R.F <= span;
+    bool ok = true;
     Task T;
     task_init(T, 0);
     for (uint32_t base = blockIdx.x * cc;;) {
-        if (base >= R.F) break;
-        const uint32_t c = min(cc, R.F - base);
+        if (base >= R.F && !phased) break;
+        const uint32_t c = (base < R.F) ? min(cc, R.F - base) : 0u;
         for (uint32_t i = threadIdx.x; i < c; i += blockDim.x) {
             uint32_t e = __ldcg(A.bag + (size_t)R.cur * A.cap + base + i);
             e = PG_DBG_ENTRY(A, e, 7u, kReach);
@@ -841,9 +855,16 @@ __device__ void cta_round(const TravArgs &A, const Round &R, const WarpSm &S, co
         // last touched in level h-1, so it is cleared here for level h+1,
         // and one CTA barrier per level suffices
         for (uint32_t h = 0;; h++) {
+            // phases: every CTA passes the barriers at depths 1, 2, 4, ... < tau
+            const bool in_phases = phased && h < R.tau;
+            if (in_phases && h > 0u && (h & (h - 1u)) == 0u &&
+                !pg_grid_sync(A.ctrl, gridDim.x, gen, A.L.timeout_ns, s_flag)) {
+                ok = false;
+                break;
+            }
             const uint32_t cl = h % 3u, nl = (h + 1u) % 3u, ql = (h + 2u) % 3u;
             const uint32_t ncur = min(Q.n[cl], QC);
-            if (ncur == 0) break;
+            if (ncur == 0 && !in_phases) break;
             T.cta_ent = Q.ent[nl];
             T.cta_aux = Q.aux[nl];
             T.cta_n = &Q.n[nl];
@@ -873,12 +894,13 @@ __device__ void cta_round(const TravArgs &A, const Round &R, const WarpSm &S, co
         }
         T.cta_n = nullptr;
         flush_spill_cta<kReach>(A, R, S, T, Q.wcnt, lane, C);
-        if (R.F <= span) break;
+        if (R.F <= span || !ok) break;
         if (threadIdx.x == 0) *Q.task = span + atomicAdd(&R.sc->head, cc);
         __syncthreads();
         base = *Q.task;
         __syncthreads();
     }
+    return ok;
 }
 
 // Edges of listed hubs, dealt in chunks of `hch` edges (hch <= hub_degree, so
@@ -1095,7 +1117,7 @@ constexpr uint32_t kRoundFeatureCap = 1u << 14;
 // Per-warp FIFO words (entry + aux per slot): only the warp local search
 // uses the FIFO, so the CTA local search leaves it out of shared memory.
 __host__ __device__ __forceinline__ uint32_t warp_fifo_words(const PgLaunch &L) {
-    return L.vgc == PG_VGC_CTA ? 0u : L.qcap;
+    return L.vgc == PG_VGC_WARP ? L.qcap : 0u;
 }
 
 template <bool kReach>
@@ -1345,8 +1367,8 @@ __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
         if (pull) {
             pull_round(A, R, S, Lvl, lane, gwarp, nwarps, C);
             pull_rounds++;
-        } else if (R.tau > 1u && A.L.vgc == PG_VGC_CTA) {
-            cta_round<kReach>(A, R, S, Q, lane, wib, nwib, C);
+        } else if (R.tau > 1u && A.L.vgc != PG_VGC_WARP) {
+            if (!cta_round<kReach>(A, R, S, Q, lane, wib, nwib, C, gen, &s_flag)) break;
             hub_edges<kReach>(A, R, S, lane, C);
         } else {
             // first task of every warp assigned statically, the rest grabbed

@@ -248,3 +248,64 @@ def test_batched_bfs_barrier_timeout_is_reported_and_recoverable(pg):
     assert e.value.status == pg.PG_ERR_TIMEOUT
     D = pg.to_uint32(G.bfs_multi(srcs))
     assert np.array_equal(D, oracle.bfs_multi(g, srcs))
+
+
+MULTI_FRONTIER = [
+    ("knn", lambda: gg.knn(150_001, 5, 2), False),
+    ("rmat", lambda: gg.rmat(16, 16, 3), False),
+    ("dgrid", lambda: gg.dgrid(301, 277, 4), True),
+    ("grid", lambda: gg.grid(400, 311), False),
+]
+
+
+@pytest.mark.parametrize("name,make,directed", MULTI_FRONTIER, ids=[m[0] for m in MULTI_FRONTIER])
+@pytest.mark.parametrize("ell", [True, False])
+def test_multi_frontier_buckets_vs_oracle(pg, name, make, directed, ell):
+    """The multiple-frontier local search (PG_VGC_BUCKETS: phases at depths
+    1, 2, 4, ... < tau with a grid barrier between them) gives the oracle's
+    distances for every tau, with hubs split and with a small CTA queue
+    (rounds whose frontier exceeds the CTAs' buffers run unphased)."""
+    g = make()
+    G = pg.Graph.from_graphgen(g, ell=ell)
+    for s in gg.pick_sources(g, 2, 13):
+        want = oracle.bfs(g, int(s))
+        for kw in ({"tau": 2}, {"tau": 8}, {"tau": 16}, {"tau": 64}, {"tau": 64, "cta_queue": 64},
+                   {"tau": 16, "hub_degree": 64}, {"tau": 32, "direction": 1}):
+            d, st = _bfs(pg, G, int(s), vgc_mode=pg.PG_VGC_BUCKETS, **kw)
+            assert _first_diff(d, want) is None, (name, int(s), kw, _first_diff(d, want))
+
+
+def test_multi_frontier_schedules_and_reach(pg):
+    """Scripted and random per-round actions with the multiple-frontier
+    search; tiny graphs from every source; reachability masks."""
+    g = gg.knn(60_000, 4, 9)
+    G = pg.Graph.from_graphgen(g, ell=True)
+    want = oracle.bfs(g, 5)
+    rng = np.random.default_rng(4)
+    for trial in range(8):
+        script = rng.integers(0, pg.PG_NUM_ACTIONS, size=int(rng.integers(1, 40))).astype(np.uint8)
+        cfg = pg.default_config(schedule=pg.PG_SCHED_SCRIPT, script_len=len(script),
+                                vgc_mode=pg.PG_VGC_BUCKETS)
+        cfg.script = script.ctypes.data
+        assert _first_diff(pg.to_uint32(G.bfs(5, cfg=cfg)), want) is None, (trial, script.tolist())
+    for seed in range(4):
+        d, _ = _bfs(pg, G, 5, schedule=pg.PG_SCHED_RANDOM, seed=seed, vgc_mode=pg.PG_VGC_BUCKETS)
+        assert _first_diff(d, want) is None, seed
+    for t in _tiny():
+        T = pg.Graph.from_graphgen(t)
+        for s in range(0, t.n, max(1, t.n // 5)):
+            d, _ = _bfs(pg, T, s, tau=8, vgc_mode=pg.PG_VGC_BUCKETS)
+            assert _first_diff(d, oracle.bfs(t, s)) is None, (t.name, s)
+        T.free()
+    h = gg.dgrid(90, 110, 6, shortcuts=9)
+    H = pg.Graph.from_graphgen(h, ell=True)
+    srcs = gg.pick_sources(h, 64, 2)
+    f, b = H.reach_multi(srcs, pg.PG_FWD | pg.PG_BWD,
+                         cfg=pg.default_config(tau=16, vgc_mode=pg.PG_VGC_BUCKETS))
+    assert np.array_equal(pg.to_uint64(f), oracle.reach(h, srcs))
+    assert np.array_equal(pg.to_uint64(b), oracle.reach(h, srcs, backward=True))
+    w = pg.trained_weights()
+    if w is not None:
+        G.set_schedule_weights(w)
+        d, _ = _bfs(pg, G, 5, schedule=pg.PG_SCHED_LEARNED, vgc_mode=pg.PG_VGC_BUCKETS)
+        assert _first_diff(d, want) is None
