@@ -356,6 +356,32 @@ def other_configs(pg, gg, peak, steps, warm, with_oracle):
     del G
     torch.cuda.empty_cache()
 
+    # ---- next row f3: weighted shortest paths on the C2 graph (seeded
+    # weights 1..1000 per undirected edge), stepping framework with VGC
+    g = gg.knn_10m()
+    wts = gg.edge_weights(g, 1, 1000, 2)
+    G = pg.Graph.from_graphgen(g)
+    G.set_weights(wts)
+    dsp = torch.empty(g.n, dtype=torch.int64, device="cuda")
+    ms_s, st_s = best(lambda st: G.sssp(0, out=dsp, stats=st))
+    Bs = 4 * (g.n + 1) + 8 * g.m + 8 * g.n
+    ss = {"n": g.n, "m": g.m, "weights": "seeded uniform 1..1000 per undirected edge",
+          "ms": ms_s, "rounds": st_s.rounds, "expansions_per_vertex": st_s.expansions / g.n,
+          "gteps": g.m / ms_s / 1e6,
+          "roofline": {"bound": "hbm", "algorithmic_bytes": Bs, "achieved": Bs / (ms_s * 1e-3) / 1e9,
+                       "peak": peak, "unit": "GB/s", "frac": Bs / (ms_s * 1e-3) / 1e9 / peak,
+                       "bytes": "4(n+1) + 4m indices + 4m weights + 8n distances"}}
+    if with_oracle:
+        import oracle
+        t0 = time.perf_counter()
+        want = oracle.sssp(g, wts, 0)
+        t_or = time.perf_counter() - t0
+        ss["exact_vs_oracle"] = bool(np.array_equal(pg.to_uint64(dsp), want))
+        ss["cpu_oracle"] = {"ms": t_or * 1e3, "cores": 1, "sample": "full workload, one Dijkstra run"}
+    res["f3 sssp knn_10m"] = ss
+    del G, dsp, wts
+    torch.cuda.empty_cache()
+
     # ---- C1 and C5 held-out kNN: plain tau 16, tau 64, learned
     for name, make in (("C1 grid_1000", gg.grid_1000), ("C5 knn_30m_k3", gg.knn_30m_k3)):
         g = make()

@@ -55,7 +55,10 @@ typedef enum pg_status {
 #define PG_SCHED_FIXED 0u   /* fixed tau; push/pull by the Beamer test if direction = AUTO */
 #define PG_SCHED_LEARNED 1u /* per-round action from the schedule MLP (weights required), judged
                                against the fixed push action tau = cfg->tau: the network's choice
-                               is taken only when its predicted gain exceeds a margin */
+                               is taken only when its predicted gain exceeds a margin.  Round r's
+                               action comes from round r-1's inputs (the network is evaluated by
+                               one warp while the round-end barrier waits); round 0's from its
+                               own inputs, known before the first barrier */
 #define PG_SCHED_RANDOM 2u  /* uniformly random action per round (trace collection) */
 #define PG_SCHED_SCRIPT 3u  /* per-round action read from cfg->script (tests) */
 
@@ -211,6 +214,9 @@ pg_status pg_reach_multi(pg_graph *g, const uint32_t *sources, uint32_t k, uint3
  * Batched BFS from k <= 64 sources in one bit-parallel level-synchronous
  * launch (all sources share each round of Algorithm 1).
  *  dist_out: k*n uint32, source-major (dist_out[j*n + v]), device or host.
+ *  cfg: direction, alpha, beta, blocks_per_sm, timeout_ms, max_rounds,
+ *    test_stall_block, and hub_degree = edges per chunk of a vertex with at
+ *    least 32 edges (0 = 1024; the chunk lists are rebuilt when it changes).
  *  Result equals k independent pg_bfs calls.
  */
 pg_status pg_bfs_multi(pg_graph *g, const uint32_t *sources, uint32_t k, uint32_t *dist_out,
@@ -254,8 +260,8 @@ pg_status pg_graph_set_weights(pg_graph *g, const uint32_t *weights, void *strea
  * entries below L + delta (L = the frontier's smallest tentative distance;
  * cfg->delta, 0 = 8 x the mean weight) and keeps the others; a warp's local
  * search expands its own improvements below the threshold (up to
- * cfg->tau x 32 per task) and queues the rest.  The result is exact for
- * every delta and tau.
+ * cfg->tau x 8 per task of 32 entries) and queues the rest.  The result is
+ * exact for every delta and tau.
  *  dist_out: n uint64, device or host memory.  cfg: tau, delta,
  *  threads_per_block, blocks_per_sm, local_queue, timeout_ms, max_rounds,
  *  test_stall_block are used; NULL = defaults.  stats: rounds, expansions,
@@ -294,11 +300,17 @@ pg_status pg_mlp_adam(float *params, const float *grad, float *m, float *v, uint
                       uint32_t t, float lr, float beta1, float beta2, float eps, void *stream);
 
 /*
- * Autotuner: times candidate launch shapes (CTAs per SM, threads per CTA,
- * local queue size, task chunk, tau) for the given traversal on g and
- * writes the fastest into *cfg (other fields kept).  kind: 0 = pg_bfs from
- * sources[0], 1 = pg_reach_multi (dir) from sources[0..k).  trials: timed
- * runs per candidate (>= 1).  Output buffers are allocated internally.
+ * Autotuner: coordinate descent over timed candidates for the given
+ * traversal on g; writes the fastest into *cfg (other fields kept).
+ *  kind 0 = pg_bfs from sources[0], 1 = pg_reach_multi (dir) from
+ *    sources[0..k): local-search organisation, tau, task chunk, local and
+ *    CTA queue sizes, threads per CTA, CTAs per SM and hub_degree (the
+ *    out-degree from which a vertex's edges are split across warps);
+ *  kind 2 = pg_bfs_multi from sources[0..k): hub_degree (there: edges per
+ *    chunk of a vertex with >= 32 edges), alpha (push -> pull threshold) and
+ *    CTAs per SM.
+ * trials: timed runs per candidate (>= 1).  Output buffers are allocated
+ * internally (kind 2: k x n uint32).
  */
 pg_status pg_autotune(pg_graph *g, uint32_t kind, const uint32_t *sources, uint32_t k,
                       uint32_t dir, uint32_t trials, pg_config *cfg, void *stream);

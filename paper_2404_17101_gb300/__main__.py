@@ -5,6 +5,8 @@
     python -m paper_2404_17101_gb300 reach --input g.adj --sources 0,5,9 [--directed] [--out masks.u64]
     python -m paper_2404_17101_gb300 scc   --input g.adj [--directed] [--out labels.u32]
     python -m paper_2404_17101_gb300 bfs64 --input g.adj [--sources ...] [--out dist.u32]
+    python -m paper_2404_17101_gb300 sssp  --input g.adj [--weights w.u32 | --wmax 1000 --wseed 1]
+                                           [--source 0] [--delta 0] [--out dist.u64]
 
 `--input` reads the PBBS "AdjacencyGraph" text format, or the GBBS binary
 layout when the file name ends in `.bin`; `--workload` takes a
@@ -12,7 +14,9 @@ named generator of the graphgen module instead (e.g. knn_10m, grid_1000).
 One JSON line with the device time (kernel events), rounds and, for BFS, the
 traversed edges and GTEPS is printed; `--out` writes the result as raw
 little-endian integers (uint32 distances / labels, uint64 masks: forward, then
-backward; bfs64: 64 x n distances, source-major).  Without --sources, reach
+backward; bfs64: 64 x n distances, source-major; sssp: uint64 distances).
+sssp reads one uint32 weight per arc (CSR order) from --weights, or draws
+seeded weights in 1..wmax per undirected edge.  Without --sources, reach
 and bfs64 take 64 seeded sources of out-degree > 0.  Needs a CUDA GPU; there
 is no CPU fallback.
 """
@@ -33,7 +37,7 @@ if ROOT not in sys.path:
 def _args(argv):
     ap = argparse.ArgumentParser(prog="python -m paper_2404_17101_gb300",
                                  description="Exact BFS, reachability and SCC on one GB300.")
-    ap.add_argument("op", choices=["bfs", "reach", "scc", "bfs64"])
+    ap.add_argument("op", choices=["bfs", "reach", "scc", "bfs64", "sssp"])
     src = ap.add_mutually_exclusive_group(required=True)
     src.add_argument("--input", help="graph file: PBBS AdjacencyGraph text, or GBBS binary (*.bin)")
     src.add_argument("--workload", help="named graphgen generator, e.g. knn_10m, grid_1000, dgrid_4000")
@@ -44,6 +48,10 @@ def _args(argv):
     ap.add_argument("--tau", type=int, default=0, help="VGC hop window (0 = library default)")
     ap.add_argument("--learned", action="store_true", help="bfs: learned per-round schedule")
     ap.add_argument("--no-ell", action="store_true", help="no padded rows (CSR only)")
+    ap.add_argument("--weights", help="sssp: raw little-endian uint32 weight per arc (CSR order)")
+    ap.add_argument("--wmax", type=int, default=1000, help="sssp: seeded weights in 1..wmax")
+    ap.add_argument("--wseed", type=int, default=1, help="sssp: seed of the weights")
+    ap.add_argument("--delta", type=int, default=0, help="sssp: step width (0 = automatic)")
     ap.add_argument("--out", help="write the result as raw little-endian integers")
     return ap.parse_args(argv)
 
@@ -94,6 +102,19 @@ def main(argv=None) -> int:
         lab, it = G.scc(cfg=pg.default_config(**kw), stats=st)
         out = pg.to_uint32(lab)
         rec.update(components=int(len(np.unique(out))), iterations=it)
+    elif a.op == "sssp":
+        if a.weights:
+            w = np.fromfile(a.weights, dtype="<u4")
+            if len(w) != g.m:
+                print(f"error: {len(w)} weights for {g.m} arcs", file=sys.stderr)
+                return 2
+        else:
+            w = gg.edge_weights(g, 1, a.wmax, a.wseed)
+        G.set_weights(w)
+        d = G.sssp(a.source, cfg=pg.default_config(delta=a.delta, **kw), stats=st)
+        out = pg.to_uint64(d)
+        rec.update(source=a.source, reached=int((out != np.uint64(0xFFFFFFFFFFFFFFFF)).sum()),
+                   expansions=st.expansions)
     rec.update(ms=st.kernel_ms, rounds=st.rounds)
     if a.out:
         out.astype(out.dtype.newbyteorder("<")).tofile(a.out)

@@ -747,7 +747,10 @@ extern "C" pg_status pg_bfs_multi(pg_graph *g, const uint32_t *sources, uint32_t
         if (st) return st;
         dev = (uint32_t *)p;
     }
-    st = pg_launch_msbfs(g, L, sources, k, dev, s);
+    // edges per chunk of a heavy vertex: cfg->hub_degree when given
+    const uint32_t clen = cfg ? cfg->hub_degree : 0u;
+    if (clen > (1u << 20)) return pg_set_error(PG_ERR_INVALID_ARG, "hub_degree %u too large", clen);
+    st = pg_launch_msbfs(g, L, sources, k, clen, dev, s);
     if (st) return st;
     if (host_out) PG_CK(cudaMemcpyAsync(dist_out, dev, bytes, cudaMemcpyDeviceToHost, s));
     return pg_finish_call(g, L, cfg, stats, s);

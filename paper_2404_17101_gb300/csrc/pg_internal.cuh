@@ -40,7 +40,7 @@ struct alignas(128) PgCtrl {
     unsigned status;               // PG_DEV_* bits
     unsigned rounds;               // rounds executed
     unsigned pull_rounds;
-    unsigned pad1;
+    unsigned next_action;          // learned schedule: the action CTA 0 chose for the next round
     unsigned long long pushes;
     unsigned long long expansions;
     unsigned long long round_t[4];   // CTA 0's clock at the start of round r (entry r % 4)
@@ -237,7 +237,7 @@ pg_status pg_launch_traverse(pg_graph *g, PgLaunch &L, int kind, uint32_t src,
                              uint32_t *dist, unsigned long long *fwd, unsigned long long *bwd,
                              cudaStream_t s);
 pg_status pg_launch_msbfs(pg_graph *g, PgLaunch &L, const uint32_t *sources, uint32_t k,
-                          uint32_t *dist, cudaStream_t s);
+                          uint32_t chunk_len, uint32_t *dist, cudaStream_t s);
 
 // BFS launch on caller-provided workspace (used by the allocation-free entry
 // point): CSR, output and every scratch buffer are given as raw pointers.

@@ -32,7 +32,9 @@
 // High-degree splitting (the load balance of Sec. 2.1's small-task
 // discussion): a vertex with at least kHeavy edges in a direction is never
 // expanded by one thread or one warp alone.  Its list is cut into chunks of
-// at most kChunk edges, listed once per graph, and any warp takes a chunk:
+// at most `chunk_len` edges (cfg->hub_degree, default 1024; the chunk lists
+// are rebuilt when it changes), listed once per graph, and any warp takes a
+// chunk:
 // top-down ORs the vertex's bits into the chunk's targets, bottom-up ORs the
 // chunk's visit words (32 at a time, stopping once every missing bit is
 // found) into next[w] with one atomicOr, and a short pass over the heavy
@@ -41,7 +43,7 @@
 
 namespace {
 constexpr uint32_t kHeavy = 32;    // edges: below, one thread (bottom-up) / one lane (top-down)
-constexpr uint32_t kChunk = 1024;  // edges per chunk of a heavy vertex
+constexpr uint32_t kChunkDefault = 1024;  // edges per chunk of a heavy vertex
 constexpr uint32_t kGather = 8;    // bottom-up: in-neighbour gathers in flight per light vertex
 constexpr uint32_t kPlanes = 5;    // distance bit-planes: distances 0..30, code 31 = written directly
 constexpr uint32_t kDirect = (1u << kPlanes) - 1u;
@@ -66,6 +68,7 @@ struct PgMsbfsWork {
     uint32_t n;
     uint2 *chunks[2];            // (vertex, first edge) per chunk: out-lists, in-lists
     uint32_t nchunks[2];
+    uint32_t chunk_len;          // edges per chunk the lists were built for
 };
 
 void pg_msbfs_release(pg_graph *g) {
@@ -84,26 +87,27 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-// chunks of each heavy vertex: cnt[v] = ceil(deg / kChunk) when deg >= kHeavy
-__global__ void k_chunk_count(const uint32_t *off, uint32_t n, uint32_t *cnt) {
+// chunks of each heavy vertex: cnt[v] = ceil(deg / clen) when deg >= kHeavy
+__global__ void k_chunk_count(const uint32_t *off, uint32_t n, uint32_t clen, uint32_t *cnt) {
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += stride) {
         uint32_t c = 0;
         if (v < n) {
             const uint32_t d = off[v + 1] - off[v];
-            c = d >= kHeavy ? (d + kChunk - 1) / kChunk : 0u;
+            c = d >= kHeavy ? (d + clen - 1) / clen : 0u;
         }
         cnt[v] = c;
     }
 }
 
-__global__ void k_chunk_fill(const uint32_t *off, uint32_t n, const uint32_t *pos, uint2 *chunks) {
+__global__ void k_chunk_fill(const uint32_t *off, uint32_t n, uint32_t clen, const uint32_t *pos,
+                             uint2 *chunks) {
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
         const uint32_t b = off[v], d = off[v + 1] - b;
         if (d < kHeavy) continue;
-        const uint32_t c = (d + kChunk - 1) / kChunk;
-        for (uint32_t i = 0; i < c; i++) chunks[pos[v] + i] = make_uint2(v, b + i * kChunk);
+        const uint32_t c = (d + clen - 1) / clen;
+        for (uint32_t i = 0; i < c; i++) chunks[pos[v] + i] = make_uint2(v, b + i * clen);
     }
 }
 
@@ -122,6 +126,7 @@ struct MsArgs {
     uint32_t alpha, beta, allow_pull, direction;
     unsigned long long timeout_ns;
     uint32_t max_rounds, stall_block;
+    uint32_t clen;        // edges per chunk of a heavy vertex
 };
 
 __device__ __forceinline__ unsigned long long wsum(unsigned long long x) {
@@ -186,6 +191,7 @@ __global__ void __launch_bounds__(512) pg_msbfs_kernel(const MsArgs A) {
         A.flev[v] = 0;
         for (uint32_t p = 0; p < kPlanes; p++) A.planes[(size_t)p * n + v] = 0;
     }
+
     if (gtid == 0) {
         // the first frontier: the distinct sources
         uint32_t F = 0;
@@ -298,7 +304,7 @@ __global__ void __launch_bounds__(512) pg_msbfs_kernel(const MsArgs A) {
                 const uint32_t w = ch.x;
                 const unsigned long long need = full & ~__ldcg(A.seen + w);
                 if (!need) continue;
-                const uint32_t e = min(ch.y + kChunk, __ldg(A.G.toff + w + 1));
+                const uint32_t e = min(ch.y + A.clen, __ldg(A.G.toff + w + 1));
                 unsigned long long acc = 0;
                 for (uint32_t q = ch.y; q < e; q += 32u) {
                     if (q + lane < e) acc |= __ldcg(visit_cur + __ldg(A.G.tidx + q + lane));
@@ -388,7 +394,7 @@ __global__ void __launch_bounds__(512) pg_msbfs_kernel(const MsArgs A) {
                 if (__ldcg(A.flev + ch.x) != L) continue;
                 const unsigned long long bits = __ldcg(visit_cur + ch.x);
                 if (!bits) continue;
-                const uint32_t e = min(ch.y + kChunk, __ldg(A.G.off + ch.x + 1));
+                const uint32_t e = min(ch.y + A.clen, __ldg(A.G.off + ch.x + 1));
                 for (uint32_t q0 = ch.y; q0 < e; q0 += 32u) {
                     const uint32_t q = q0 + (uint32_t)lane;
                     uint32_t w = 0;
@@ -461,15 +467,15 @@ __global__ void k_msbfs_decode(const unsigned long long *seen, const unsigned lo
 }  // namespace
 
 // The chunk list of one direction (built once per graph, on first use).
-static pg_status build_chunks(pg_graph *g, const uint32_t *off, uint2 **out, uint32_t *count,
-                              cudaStream_t s) {
+static pg_status build_chunks(pg_graph *g, const uint32_t *off, uint32_t clen, uint2 **out,
+                              uint32_t *count, cudaStream_t s) {
     const uint32_t n = g->n;
     *out = nullptr;
     *count = 0;
     uint32_t *cnt = nullptr;
     PG_CK(cudaMallocAsync(&cnt, ((size_t)n + 1) * 2 * sizeof(uint32_t), s));
     uint32_t *pos = cnt + n + 1;
-    k_chunk_count<<<g->num_sms * 4, 256, 0, s>>>(off, n, cnt);
+    k_chunk_count<<<g->num_sms * 4, 256, 0, s>>>(off, n, clen, cnt);
     PG_CK(cudaGetLastError());
     pg_status st = pg_exclusive_scan(cnt, pos, n + 1, s);
     if (st) return st;
@@ -478,7 +484,7 @@ static pg_status build_chunks(pg_graph *g, const uint32_t *off, uint2 **out, uin
     PG_CK(cudaStreamSynchronize(s));
     uint2 *ch = nullptr;
     PG_CK(cudaMalloc(&ch, (size_t)(total ? total : 1) * sizeof(uint2)));
-    if (total) k_chunk_fill<<<g->num_sms * 4, 256, 0, s>>>(off, n, pos, ch);
+    if (total) k_chunk_fill<<<g->num_sms * 4, 256, 0, s>>>(off, n, clen, pos, ch);
     PG_CK(cudaGetLastError());
     PG_CK(cudaFreeAsync(cnt, s));
     *out = ch;
@@ -487,7 +493,18 @@ static pg_status build_chunks(pg_graph *g, const uint32_t *off, uint2 **out, uin
 }
 
 pg_status pg_launch_msbfs(pg_graph *g, PgLaunch &L, const uint32_t *sources, uint32_t k,
-                          uint32_t *dist, cudaStream_t s) {
+                          uint32_t chunk_len, uint32_t *dist, cudaStream_t s) {
+    const uint32_t clen = chunk_len ? chunk_len : kChunkDefault;
+    if (g->msbfs && g->msbfs->chunk_len != clen) {
+        // another chunk length: rebuild the chunk lists (the words are kept)
+        PgMsbfsWork &W = *g->msbfs;
+        PG_CK(cudaStreamSynchronize(s));
+        cudaFree(W.chunks[0]);
+        if (W.chunks[1] != W.chunks[0]) cudaFree(W.chunks[1]);
+        W.chunks[0] = W.chunks[1] = nullptr;
+        W.nchunks[0] = W.nchunks[1] = 0;
+        W.chunk_len = 0;
+    }
     if (!g->msbfs) {
         PgMsbfsWork *W = new PgMsbfsWork();
         memset(W, 0, sizeof(PgMsbfsWork));
@@ -516,9 +533,12 @@ pg_status pg_launch_msbfs(pg_graph *g, PgLaunch &L, const uint32_t *sources, uin
         W->flev = q + 5 * n;
         W->n = g->n;
         g->msbfs = W;
+    }
+    if (g->msbfs->chunk_len == 0) {
+        PgMsbfsWork *W = g->msbfs;
         const bool self = g->transpose_is_self || !g->d_toff;
         for (int d = 0; d < (self ? 1 : 2); d++) {
-            pg_status st = build_chunks(g, d ? g->d_toff : g->d_off, &W->chunks[d], &W->nchunks[d], s);
+            pg_status st = build_chunks(g, d ? g->d_toff : g->d_off, clen, &W->chunks[d], &W->nchunks[d], s);
             if (st) {
                 pg_msbfs_release(g);
                 return st;
@@ -528,6 +548,7 @@ pg_status pg_launch_msbfs(pg_graph *g, PgLaunch &L, const uint32_t *sources, uin
             W->chunks[1] = W->chunks[0];
             W->nchunks[1] = W->nchunks[0];
         }
+        W->chunk_len = clen;
     }
     PgMsbfsWork &W = *g->msbfs;
     MsArgs A;
@@ -565,6 +586,7 @@ pg_status pg_launch_msbfs(pg_graph *g, PgLaunch &L, const uint32_t *sources, uin
     A.timeout_ns = L.timeout_ns;
     A.max_rounds = L.max_rounds;
     A.stall_block = L.stall_block;
+    A.clen = clen;
     const uint32_t threads = 512;
     int per_sm = 0;
     PG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pg_msbfs_kernel, threads, 0));

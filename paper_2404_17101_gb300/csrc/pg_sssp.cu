@@ -7,13 +7,13 @@
 // below theta are expanded (every out-arc relaxed with a 64-bit atomicMin on
 // the target's distance); entries at or above theta are kept for a later
 // round.  With VGC a warp keeps expanding, in a shared-memory FIFO, the
-// vertices its own relaxations improve below theta (up to tau x 32 local
-// expansions per task), so one round covers many hops of a step; every
-// other improvement goes to the next bag (one entry per vertex and round,
-// de-duplicated by a round tag).  Every improvement is expanded or queued,
-// so when the bag is empty every arc satisfies dist[x] <= dist[u] + w(u, x)
-// and every distance is a real path length: the exact shortest-path
-// distances, whatever delta and tau.
+// vertices its own relaxations improve below theta (up to tau x 8 local
+// expansions per task of 32 frontier entries), so one round covers many
+// hops of a step; every other improvement goes to the next bag (one entry
+// per vertex and round, de-duplicated by a round tag).  Every improvement is
+// expanded or queued, so when the bag is empty every arc satisfies
+// dist[x] <= dist[u] + w(u, x) and every distance is a real path length:
+// the exact shortest-path distances, whatever delta and tau.
 #include "pg_internal.cuh"
 
 namespace {
@@ -425,7 +425,7 @@ extern "C" pg_status pg_sssp(pg_graph *g, uint32_t src, uint64_t *dist_out, cons
     A.cnt = W.cnt;
     A.src = src;
     A.delta = delta;
-    A.budget = tau * 32u;
+    A.budget = tau * 8u;
     A.qcap = qcap;
     A.timeout_ns = (unsigned long long)(c->timeout_ms ? c->timeout_ms : 5000) * 1000000ull;
     A.max_rounds = c->max_rounds;

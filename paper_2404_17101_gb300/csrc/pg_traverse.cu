@@ -1124,7 +1124,6 @@ template <bool kReach>
 __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_flag;
-    __shared__ uint32_t s_action;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int nwib = blockDim.x >> 5;
@@ -1171,7 +1170,8 @@ __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
         s_cs.max_level = 0;
     }
 
-    if (A.L.schedule == PG_SCHED_LEARNED)
+    // the network runs in CTA 0 only (see the round-end decision below)
+    if (A.L.schedule == PG_SCHED_LEARNED && blockIdx.x == 0)
         for (int i = threadIdx.x; i < (int)PG_MLP_NPARAMS; i += blockDim.x) {
             // W2 (32 x 32) and W3 (8 x 32) are stored transposed, so that in
             // mlp_decide the lanes read consecutive words (no bank conflicts)
@@ -1200,6 +1200,9 @@ __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
             if (A.dir & PG_BWD) A.mask1[v] = bits;
         }
     }
+    // the fixed schedule's push action: tau = 2^a_fix (rounded down, at most 64)
+    const uint32_t a_fix = min(31u - (uint32_t)__clz((int)max(A.L.tau, 1u)), 6u);
+    __shared__ unsigned long long s_init[2];  // CTA 0: size and out-edges of the first bag
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         for (int s = 0; s < PG_NUM_SLOTS; s++) reset_slot(&ctrl->slot[s]);
         PgSlot *s0 = &ctrl->slot[0];
@@ -1234,6 +1237,21 @@ __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
         s0->min_level = 0;
         s0->max_level = 0;
         s0->out_edges = oe;
+        s_init[0] = cnt;
+        s_init[1] = oe;
+    }
+    // learned schedule, round 0: CTA 0 built the first bag, so it knows round
+    // 0's inputs already and picks round 0's action before the first barrier
+    // (later rounds: at the end of the previous round, below)
+    if (A.L.schedule == PG_SCHED_LEARNED && blockIdx.x == 0) {
+        __syncthreads();
+        if (wib == 0) {
+            const float F0 = (float)s_init[0], E0 = (float)s_init[1];
+            const float x0[5] = {flog2p1(F0) / 24.f, flog2p1(E0) / 32.f, flog2p1(E0 / F0) / 8.f,
+                                 flog2p1(0.f) / 24.f, flog2p1(0.f) / 16.f};
+            const uint32_t a = mlp_decide(s_w, x0, (!kReach) && A.L.allow_pull, a_fix, lane);
+            if (lane == 0) ctrl->next_action = a;
+        }
     }
     if (A.L.stall_block == blockIdx.x) return;  // fault injection: never arrive
     if (!pg_grid_sync(ctrl, nblocks, gen, tmo, &s_flag)) return;
@@ -1251,7 +1269,7 @@ __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
     unsigned long long t_round = 0;
     // the round's control words, read once per CTA (thread 0) and shared
     __shared__ unsigned long long s_in[5];
-    __shared__ uint32_t s_in32[4];
+    __shared__ uint32_t s_in32[5];
     for (;; r++) {
         Round R;
         R.cur = r & 1u;
@@ -1267,6 +1285,7 @@ __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
             s_in[0] = pg_ldcg64(&R.sc->out_edges);
             s_in[1] = pg_ldcg64(&R.sc->hub_pack);
             s_in32[3] = (r > 0) ? __ldcg(&ctrl->exp_verts[(r - 1) & 3]) : 0u;
+            s_in32[4] = __ldcg(&ctrl->next_action);
             s_in[2] = (r > 0) ? pg_ldcg64(&ctrl->exp_edges[(r - 1) & 3]) : 0ull;
             s_in[3] = (r >= 2) ? pg_ldcg64(&ctrl->round_t[(r - 1) & 3]) : 0ull;
             s_in[4] = (r >= 2) ? pg_ldcg64(&ctrl->round_t[(r - 2) & 3]) : 0ull;
@@ -1295,7 +1314,7 @@ __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
         // previous-round time as published by CTA 0 (visible one round late)
         const unsigned long long prev_ns = (r >= 2) ? s_in[3] - s_in[4] : 0ull;
         float x[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        if (A.L.schedule == PG_SCHED_LEARNED || A.L.trace != nullptr) {
+        if ((A.L.schedule == PG_SCHED_LEARNED || A.L.trace != nullptr) && blockIdx.x == 0) {
             x[0] = flog2p1((float)R.F) / 24.f;
             x[1] = flog2p1((float)E) / 32.f;
             x[2] = flog2p1((float)E / (float)R.F) / 8.f;
@@ -1307,14 +1326,10 @@ __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
         const bool can_pull = (!kReach) && A.L.allow_pull && Lvl != PG_INF;
         uint32_t action;
         if (A.L.schedule == PG_SCHED_LEARNED) {
-            if (wib == 0) {
-                // the fixed schedule's push action: tau = 2^a_fix (rounded down, at most 64)
-                const uint32_t a_fix = min(31u - (uint32_t)__clz((int)max(A.L.tau, 1u)), 6u);
-                const uint32_t a = mlp_decide(s_w, x, can_pull, a_fix, lane);
-                if (lane == 0) s_action = a;
-            }
-            __syncthreads();
-            action = s_action;
+            // chosen by CTA 0 at the end of the previous round from that
+            // round's features (round 0: from round 0's, before the first barrier)
+            action = s_in32[4];
+            if (action >= PG_NUM_ACTIONS || (action == PG_ACTION_PULL && !can_pull)) action = a_fix;
         } else if (A.L.schedule == PG_SCHED_RANDOM) {
             const uint32_t na = can_pull ? PG_NUM_ACTIONS : PG_NUM_ACTIONS - 1u;
             action = mix32(A.L.seed, r) % na;
@@ -1398,6 +1413,13 @@ __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
             }
             C.exp_edges = 0;
             C.exp_verts = 0;
+        }
+        // learned schedule: CTA 0's warp 0 picks the next round's action from
+        // this round's features while it waits for the slowest CTA; the
+        // barrier below publishes it with the round's other control words
+        if (A.L.schedule == PG_SCHED_LEARNED && blockIdx.x == 0 && wib == 0) {
+            const uint32_t a = mlp_decide(s_w, x, (!kReach) && A.L.allow_pull, a_fix, lane);
+            if (lane == 0) ctrl->next_action = a;
         }
         // the CTA's aggregates reach the global counters before its arrival
         PgSlot *sn = R.sn;

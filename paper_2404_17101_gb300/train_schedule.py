@@ -16,7 +16,12 @@ actions.  Each rerun records the five features of round r.  The label of
 action a at that state is -log2(T_a / min_b T_b), T = kernel time of the
 whole run, so the network learns which action is best from here on; the
 traversal re-decides every round and takes the arg-max (one step of policy
-improvement over the fixed-tau base).  Forward, backward and Adam run in the
+improvement over the fixed-tau base).  The traversal decides round r >= 1
+from round r - 1's features (the network runs at the barrier that ends round
+r - 1), so the state of round r is recorded as round r - 1's features; round
+0 is decided from round 0's own features, and since round 1 is then decided
+from the same input, its state is not sampled (round 0's label, an action held
+from round 0 on, is the one that input decides).  Forward, backward and Adam run in the
 library's own CUDA kernels (pg_mlp_forward / pg_mlp_backward / pg_mlp_adam).
 
     python -m paper_2404_17101_gb300.train_schedule --out schedule_mlp.f32 [--quick]
@@ -43,28 +48,33 @@ INF = 0xFFFFFFFF
 
 
 def training_graphs(quick: bool):
-    """Seeded training families: grids (aspect 1:1 .. 1:1000), kNN (k 2..10), R-MAT
-    and path-like strips."""
+    """Seeded training families: grids (aspect 1:1 .. 1:1000, up to 16M
+    vertices), kNN (k 2..10, up to 20M points), R-MAT (scale 18..22) and
+    path-like strips.  None of them is an evaluation graph: the held-out
+    graphs (kNN 30M k = 3 seed 5, the 1 x 20M strip, and the gain test's
+    1100 x 900 grid, 1 x 200k strip, R-MAT 18 seed 903 and kNN 2M k = 3 seed
+    902) use other sizes or seeds, and so do the benchmark graphs."""
     fams = [
-        ("grid_1000x1000", lambda: gg.grid(1000, 1000)),
+        ("grid_2000x2000", lambda: gg.grid(2000, 2000)),
         ("grid_300x3000", lambda: gg.grid(300, 3000)),
         ("grid_60x20000", lambda: gg.grid(60, 20000)),
         ("knn_1m_k5", lambda: gg.knn(1_000_000, 5, 101)),
         ("knn_1m_k3", lambda: gg.knn(1_000_000, 3, 102)),
-        ("knn_500k_k8", lambda: gg.knn(500_000, 8, 103)),
-        ("rmat_17", lambda: gg.rmat(17, 16, 104)),
+        ("rmat_18", lambda: gg.rmat(18, 16, 109)),
     ]
     if not quick:
         fams += [
-            ("grid_2000x2000", lambda: gg.grid(2000, 2000)),
-            ("grid_126x16000", lambda: gg.grid(126, 16000)),
-            ("grid_4x100000", lambda: gg.grid(4, 100_000)),
-            ("knn_4m_k5", lambda: gg.knn(4_000_000, 5, 105)),
-            ("knn_2m_k2", lambda: gg.knn(2_000_000, 2, 106)),
-            ("knn_2m_k10", lambda: gg.knn(2_000_000, 10, 107)),
-            ("knn_3m_k4", lambda: gg.knn(3_000_000, 4, 108)),
-            ("rmat_18", lambda: gg.rmat(18, 16, 109)),
+            ("grid_4000x4000", lambda: gg.grid(4000, 4000)),
+            ("grid_1000x16000", lambda: gg.grid(1000, 16000)),
+            ("grid_400x40000", lambda: gg.grid(400, 40000)),
+            ("grid_126x126000", lambda: gg.grid(126, 126_000)),
+            ("knn_20m_k5", lambda: gg.knn(20_000_000, 5, 111)),
+            ("knn_8m_k2", lambda: gg.knn(8_000_000, 2, 106)),
+            ("knn_4m_k10", lambda: gg.knn(4_000_000, 10, 107)),
+            ("knn_6m_k4", lambda: gg.knn(6_000_000, 4, 108)),
+            ("knn_3m_k7", lambda: gg.knn(3_000_000, 7, 112)),
             ("rmat_20", lambda: gg.rmat(20, 16, 110)),
+            ("rmat_22", lambda: gg.rmat(22, 16, 113)),
             # path-like strips: frontiers of one or two vertices for
             # hundreds of thousands of rounds (the adversarial chain)
             ("strip_300k", lambda: gg.strip(300_000)),
@@ -74,7 +84,8 @@ def training_graphs(quick: bool):
 
 
 # Strips are slow to roll out (one level per hop); fewer sources and states.
-FEW_STATES = {"strip_300k": (1, 5), "grid_2x150000": (1, 5)}
+FEW_STATES = {"strip_300k": (1, 5), "grid_2x150000": (1, 5), "grid_126x126000": (1, 6),
+              "grid_400x40000": (1, 8)}
 
 
 def collect(G, src, base_tau=16, points=10, reps=2, hold=80_000):
@@ -87,7 +98,9 @@ def collect(G, src, base_tau=16, points=10, reps=2, hold=80_000):
     for _ in range(reps):
         G.bfs(src, cfg=pg.default_config(tau=base_tau), stats=st)
         R = st.rounds
-    rs = sorted(set(int(R * f) for f in np.linspace(0.0, 0.9, points)))
+    # the decision for round r >= 1 sees round r - 1's features and round 0's
+    # sees its own, so rounds 0 and 1 share one input: round 1 is not sampled
+    rs = sorted(set(int(R * f) for f in np.linspace(0.0, 0.9, points)) - {1})
     Xs, As, Ys = [], [], []
     for r in rs:
         T, feat = {}, None
@@ -107,7 +120,7 @@ def collect(G, src, base_tau=16, points=10, reps=2, hold=80_000):
                 raise RuntimeError("a schedule changed the distances")
             T[a] = min(ts)
             if st.rounds > r:
-                feat = list(buf[r].features)
+                feat = list(buf[max(r - 1, 0)].features)
         if feat is None:
             continue
         best = min(T.values())
@@ -209,12 +222,14 @@ def main():
     log(f"samples {len(Y)}  collected in {time.time() - t0:.1f}s")
     W, mu, sd = train(X, A, Y, epochs=args.epochs, batch=256, log=log)
     W.astype(np.float32).tofile(args.out)
-    log(f"weights -> {args.out}")
+    log(f"weights -> {os.path.basename(args.out)}")
     if args.eval:
         for name, make in (("knn_2m_k5_heldout", lambda: gg.knn(2_000_000, 5, 901)),
                            ("knn_2m_k3_heldout", lambda: gg.knn(2_000_000, 3, 902)),
-                           ("grid_1000x1000", lambda: gg.grid(1000, 1000)),
+                           ("grid_1100x900_heldout", lambda: gg.grid(1100, 900)),
                            ("rmat_18_heldout", lambda: gg.rmat(18, 16, 903)),
+                           ("knn_10m_k5 (benchmark C2)", lambda: gg.knn_10m()),
+                           ("knn_30m_k3_heldout (benchmark C5)", lambda: gg.knn_30m_k3()),
                            ("strip_1m", lambda: gg.strip(1_000_000))):
             g = make()
             G = pg.Graph.from_graphgen(g, ell=True)

@@ -69,3 +69,21 @@ def test_bfs_on_a_gbbs_binary_file(tmp_path):
     r = _run(["bfs", "--input", p, "--directed", "--source", "11", "--out", out])
     assert r.returncode == 0, r.stderr
     assert np.array_equal(np.fromfile(out, dtype="<u4"), oracle.bfs(g, 11))
+
+
+@pytest.mark.gpu
+def test_sssp_from_the_command_line(tmp_path):
+    """sssp with a weight file and with seeded weights, against Dijkstra."""
+    g = gg.knn(20_000, 4, 6)
+    p = str(tmp_path / "g.bin")
+    gg.write_gbbs_bin(g, p)
+    w = gg.edge_weights(g, 1, 50, 3)
+    wp = str(tmp_path / "w.u32")
+    w.astype("<u4").tofile(wp)
+    out = str(tmp_path / "d.u64")
+    r = _run(["sssp", "--input", p, "--weights", wp, "--source", "9", "--out", out])
+    assert r.returncode == 0, r.stderr
+    assert np.array_equal(np.fromfile(out, dtype="<u8"), oracle.sssp(g, w, 9))
+    r = _run(["sssp", "--input", p, "--wmax", "700", "--wseed", "5", "--out", out])
+    assert r.returncode == 0, r.stderr
+    assert np.array_equal(np.fromfile(out, dtype="<u8"), oracle.sssp(g, gg.edge_weights(g, 1, 700, 5), 0))

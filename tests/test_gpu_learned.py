@@ -31,7 +31,7 @@ def _best_ms(pg, G, cfg, reps=3):
 
 # (graph, minimum speed-up of learned over plain tau = 16)
 CASES = [
-    ("grid_1000x1000", lambda: gg.grid(1000, 1000), 1.10),
+    ("grid_1100x900_heldout", lambda: gg.grid(1100, 900), 1.10),
     ("strip_1x200000", lambda: gg.strip(200_000), 1.10),
     ("rmat_18_heldout", lambda: gg.rmat(18, 16, 903), 1.10),
     ("knn_2m_k3_heldout", lambda: gg.knn(2_000_000, 3, 902), 0.90),

@@ -73,10 +73,12 @@ A_FIX = 4                        # push with the default tau = 16
 
 
 def test_in_loop_decision_matches_oracle_argmax(pg):
-    """The traversal's per-round choice is the arg-max of the network on the
-    features it recorded unless that beats the fixed-tau action by no more
-    than the judge margin (pins the in-kernel inference and the judge), and
-    the result is still exact."""
+    """The traversal's choice for round r >= 1 is the arg-max of the network on
+    the features recorded in round r - 1 (CTA 0 evaluates it while waiting at
+    the barrier that ends round r - 1), and round 0's on round 0's own
+    features (known before the first barrier), unless that beats the fixed-tau
+    action by no more than the judge margin.  This pins the in-kernel
+    inference and the judge; the result is still exact."""
     import oracle
     g = gg.knn(200_000, 5, 4)
     G = pg.Graph.from_graphgen(g)
@@ -96,15 +98,16 @@ def test_in_loop_decision_matches_oracle_argmax(pg):
         acts = np.array([buf[r].action for r in range(R)])
         Y, _ = mlp.forward(w.astype(np.float64), X.astype(np.float64))
         for r in range(R):
-            order = np.argsort(-Y[r])
-            if Y[r, order[0]] - Y[r, order[1]] < 1e-4:
+            y = Y[max(r - 1, 0)]
+            order = np.argsort(-y)
+            if y[order[0]] - y[order[1]] < 1e-4:
                 continue
-            gain = Y[r, order[0]] - Y[r, A_FIX]
+            gain = y[order[0]] - y[A_FIX]
             margin = JUDGE_DOWN if order[0] < A_FIX else JUDGE_UP
             if abs(gain - margin) < 1e-4:
                 continue
             want = order[0] if gain > margin else A_FIX
-            assert acts[r] == want, (trial, r, acts[r], order[:3], Y[r])
+            assert acts[r] == want, (trial, r, acts[r], order[:3], y)
 
 
 def test_features_match_definition(pg):

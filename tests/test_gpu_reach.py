@@ -171,3 +171,40 @@ def test_bfs_multi_direction_switching(pg, make, alpha, beta):
     D = pg.to_uint32(G.bfs_multi(srcs, cfg=pg.default_config(direction=pg.PG_DIR_AUTO, alpha=alpha,
                                                               beta=beta), stats=st))
     assert np.array_equal(D, oracle.bfs_multi(g, srcs)), (st.rounds, st.pull_rounds)
+
+
+def test_autotuned_configurations_are_exact(pg):
+    """pg_autotune picks a launch shape and tau by timing; whatever it picks,
+    the tuned configuration's output must equal the oracle's: BFS (kind 0)
+    on a kNN graph with padded rows, forward + backward reachability (kind
+    1) on a directed grid."""
+    g = gg.knn(300_000, 5, 12)
+    G = pg.Graph.from_graphgen(g, ell=True)
+    cfg = G.autotune([0], kind=0, trials=1)
+    assert cfg.tau >= 1 and cfg.threads_per_block in (0, 256, 512)
+    d = pg.to_uint32(G.bfs(0, cfg=cfg))
+    assert np.array_equal(d, oracle.bfs(g, 0)), (cfg.tau, cfg.vgc_mode, cfg.chunk)
+    h = gg.dgrid(400, 500, 7, shortcuts=20)
+    H = pg.Graph.from_graphgen(h, ell=True)
+    srcs = gg.pick_sources(h, 64, 8)
+    both = pg.PG_FWD | pg.PG_BWD
+    tuned = H.autotune(srcs, kind=1, direction=both, trials=1)
+    f, b = H.reach_multi(srcs, both, cfg=tuned)
+    assert np.array_equal(pg.to_uint64(f), oracle.reach(h, srcs)), (tuned.tau, tuned.vgc_mode)
+    assert np.array_equal(pg.to_uint64(b), oracle.reach(h, srcs, backward=True))
+
+
+def test_autotuned_batched_bfs_is_exact(pg):
+    """Kind 2 tunes the batched BFS's chunk length, alpha and CTAs per SM; the
+    tuned configuration and chunk lengths different from the default
+    (rebuilt chunk lists) give the oracle's rows."""
+    g = gg.rmat(15, 16, 31)
+    G = pg.Graph.from_graphgen(g)
+    srcs = gg.pick_sources(g, 64, 3)
+    want = oracle.bfs_multi(g, srcs)
+    tuned = G.autotune(srcs, kind=2, trials=1, cfg=pg.default_config(direction=pg.PG_DIR_AUTO))
+    assert tuned.hub_degree in (256, 512, 1024, 2048, 4096)
+    assert np.array_equal(pg.to_uint32(G.bfs_multi(srcs, cfg=tuned)), want)
+    for clen in (32, 100, 4096):
+        D = G.bfs_multi(srcs, cfg=pg.default_config(direction=pg.PG_DIR_AUTO, hub_degree=clen))
+        assert np.array_equal(pg.to_uint32(D), want), clen
