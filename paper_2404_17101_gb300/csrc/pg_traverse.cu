@@ -693,87 +693,152 @@ __device__ void expand_rows_sp(const TravArgs &A, const Round &R, const WarpSm &
 }
 
 // One level of the CTA's BFS local search over forward padded rows of width
-// W = 2^LW, in its shortest instruction path (the level's latency is the
-// warps' instruction paths plus one row read and one atomicMin round trip).
-// Lane l of a wave takes entry w0 + l / W and slot l % W of its row: it
-// relaxes at most one arc, and the children inside the
-// window are appended to the CTA's next level with one shared-memory atomic
-// per warp; the others go to the warp's spill staging.  Entries whose list
-// is in the CSR (every slot marked PG_ELL_LONG) are expanded afterwards, one
-// per lane, by the generic expand_wave.
-template <uint32_t LW>
+// W = 2^LW.  Its latency is one dependent chain per warp pass: entry (shared
+// memory), row read, atomicMin, append.  To keep the passes few, an entry
+// takes NL = 2^LS lanes (NL <= W; lane j reads slots j, j + NL, ... of the
+// row, coalesced), and a warp holds U groups of 32 / NL entries in flight:
+// every row read of the pass is issued before the first atomicMin and every
+// atomicMin before the first result is used, so a pass over up to
+// U * 32 / NL entries per warp costs about one row read and one atomic round
+// trip.  The children inside the window go to the CTA's next level with one
+// warp scan and one shared-memory atomic per pass; the others go to the
+// warp's spill staging.  Entries whose list is in the CSR (every slot marked
+// PG_ELL_LONG) are expanded afterwards, one per lane, by expand_wave.
+template <uint32_t LW, uint32_t LS, uint32_t U>
 __device__ void bfs_rows_level(const TravArgs &A, const Round &R, const WarpSm &S, Task &T,
                                const uint32_t *ents, const uint32_t *auxs, uint32_t ncur,
                                bool from_bag, int lane, int wib, int nwib, Counters &C) {
-    constexpr uint32_t W = 1u << LW, G = 32u >> LW;
-    const uint32_t j = (uint32_t)lane & (W - 1u);
+    constexpr uint32_t W = 1u << LW, NL = 1u << LS, SL = W >> LS, G = 32u >> LS;
+    static_assert(LS <= LW && SL * U <= 8u, "at most 8 arcs per lane and pass");
+    const uint32_t j = (uint32_t)lane & (NL - 1u);
     const uint32_t win = R.Lbase + R.tau;  // children at distance < win stay in the CTA
-    const unsigned lt = pg_lanemask_lt();
     const uint32_t *ell = A.ell0;
-    for (uint32_t w0 = (uint32_t)wib * G; w0 < ncur; w0 += (uint32_t)nwib * G) {
-        const uint32_t i = w0 + ((uint32_t)lane >> LW);
-        uint32_t v = PG_NONE, aux = 0, nd = PG_INF;
-        if (i < ncur) {
-            v = PG_DBG_ENTRY(A, ents[i], 10u, false);
-            aux = auxs[i];
+    const uint32_t gstride = (uint32_t)nwib * G;  // entries per CTA-wide group
+    for (uint32_t w0 = (uint32_t)wib * G; w0 < ncur; w0 += gstride * U) {
+        uint32_t v[U], nd[U], aux[U];
+#pragma unroll
+        for (uint32_t u = 0; u < U; u++) {
+            const uint32_t i = w0 + u * gstride + ((uint32_t)lane >> LS);
+            v[u] = PG_NONE;
+            aux[u] = 0;
+            nd[u] = PG_INF;
+            if (i < ncur) {
+                v[u] = PG_DBG_ENTRY(A, ents[i], 10u, false);
+                aux[u] = auxs[i];
+            }
         }
-        if (v != PG_NONE) {
-            // a local-search entry carries its distance; a bag entry reads it
-            const uint32_t d = from_bag ? pg_ldcg(A.dist + v) : aux;
-            nd = (d == PG_INF) ? PG_INF : d + 1u;
-        }
-        const bool live = nd != PG_INF;
-        uint32_t x = PG_NONE;
-        if (live) x = __ldg(ell + (size_t)v * W + j);
+#pragma unroll
+        for (uint32_t u = 0; u < U; u++)
+            if (v[u] != PG_NONE) {
+                // a local-search entry carries its distance; a bag entry reads it
+                const uint32_t d = from_bag ? pg_ldcg(A.dist + v[u]) : aux[u];
+                nd[u] = (d == PG_INF) ? PG_INF : d + 1u;
+            }
+        // every row read of the pass, then every atomicMin
+        uint32_t x[U][SL];
+#pragma unroll
+        for (uint32_t u = 0; u < U; u++)
+#pragma unroll
+            for (uint32_t s = 0; s < SL; s++) {
+                x[u][s] = PG_NONE;
+                if (nd[u] != PG_INF) x[u][s] = __ldg(ell + (size_t)v[u] * W + s * NL + j);
 #ifdef PG_DEBUG_BOUNDS
-        if (x < 0x80000000u) x = PG_DBG_ID(A, x, 11u, false);
+                if (x[u][s] < 0x80000000u) x[u][s] = PG_DBG_ID(A, x[u][s], 11u, false);
 #endif
-        const bool arc = x < 0x80000000u;  // not padding, not a CSR-row marker
-        const bool loc = nd < win;
-        uint32_t old = 0;
-        if (arc) old = atomicMin(A.dist + x, nd);
-        if (arc && loc) pg_prefetch_l1(ell + (size_t)x * W);
-        const bool imp = arc && nd < old;
-        const bool is_long = live && j == 0u && x == PG_ELL_LONG;
-        if (live && j == 0u && !is_long) { C.expansions++; C.exp_verts++; }
-        if (arc) C.exp_edges++;
-        // children inside the window: the CTA's next level
-        bool spill = imp && !loc;
-        const unsigned bl = __ballot_sync(kFull, imp && loc);
-        if (bl) {
-            uint32_t base = 0;
-            if (lane == 0) base = atomicAdd(T.cta_n, (unsigned)__popc(bl));
-            base = __shfl_sync(kFull, base, 0);
-            const uint32_t p = base + __popc(bl & lt);
-            if (imp && loc) {
-                if (p < T.cta_cap) {
-                    T.cta_ent[p] = x;
-                    T.cta_aux[p] = nd;
-                } else {
-                    spill = true;  // the level buffer is full
+            }
+        uint32_t old[U][SL];
+#pragma unroll
+        for (uint32_t u = 0; u < U; u++)
+#pragma unroll
+            for (uint32_t s = 0; s < SL; s++) {
+                old[u][s] = 0;
+                if (x[u][s] < 0x80000000u) {  // not padding, not a CSR-row marker
+                    old[u][s] = atomicMin(A.dist + x[u][s], nd[u]);
+                    if (nd[u] < win) pg_prefetch_l1(ell + (size_t)x[u][s] * W);
                 }
+            }
+        // improved children: inside the window -> next level, else spill.
+        // Bit k = u * SL + s of a lane's masks is arc (u, s); one ballot per
+        // bit gives every arc's rank, and one shared-memory atomic per pass
+        // reserves the warp's places in the next level.
+        constexpr uint32_t K = U * SL;
+        const unsigned lt = pg_lanemask_lt();
+        uint32_t locm = 0, impm = 0;
+        bool is_long[U];
+#pragma unroll
+        for (uint32_t u = 0; u < U; u++) {
+            const bool live = nd[u] != PG_INF;
+            is_long[u] = live && j == 0u && x[u][0] == PG_ELL_LONG;
+            if (live && j == 0u && !is_long[u]) { C.expansions++; C.exp_verts++; }
+#pragma unroll
+            for (uint32_t s = 0; s < SL; s++) {
+                const bool arc = x[u][s] < 0x80000000u;
+                if (arc) C.exp_edges++;
+                const bool imp = arc && nd[u] < old[u][s];
+                impm |= (imp ? 1u : 0u) << (u * SL + s);
+                locm |= (imp && nd[u] < win ? 1u : 0u) << (u * SL + s);
+            }
+        }
+        unsigned bal[K];
+        uint32_t tot = 0;
+#pragma unroll
+        for (uint32_t k = 0; k < K; k++) {
+            bal[k] = __ballot_sync(kFull, (locm >> k) & 1u);
+            tot += (uint32_t)__popc(bal[k]);
+        }
+        uint32_t spm = impm & ~locm;  // spilled arcs of this lane
+        if (tot) {
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(T.cta_n, tot);
+            base = __shfl_sync(kFull, base, 0);
+#pragma unroll
+            for (uint32_t k = 0; k < K; k++) {
+                if ((locm >> k) & 1u) {
+                    const uint32_t p = base + (uint32_t)__popc(bal[k] & lt);
+                    if (p < T.cta_cap) {
+                        T.cta_ent[p] = x[k / SL][k % SL];
+                        T.cta_aux[p] = nd[k / SL];
+                    } else {
+                        spm |= 1u << k;  // the level buffer is full
+                    }
+                }
+                base += (uint32_t)__popc(bal[k]);
             }
         }
         // children beyond the window (or overflow): the warp's spill staging
-        const unsigned bs = __ballot_sync(kFull, spill);
-        if (bs) {
-            if (T.nsp + (uint32_t)__popc(bs) > kSpillCap) flush_spill<false>(A, R, S, T, lane, C);
-            if (spill) {
-                const uint32_t p = T.nsp + __popc(bs & lt);
-                S.sp[p] = x;
-                S.spa[p] = nd;
+        if (__any_sync(kFull, spm != 0u)) {
+            unsigned sb[K];
+            uint32_t stot = 0;
+#pragma unroll
+            for (uint32_t k = 0; k < K; k++) {
+                sb[k] = __ballot_sync(kFull, (spm >> k) & 1u);
+                stot += (uint32_t)__popc(sb[k]);
             }
-            T.nsp += __popc(bs);
+            if (T.nsp + stot > kSpillCap) flush_spill<false>(A, R, S, T, lane, C);
+            uint32_t q = T.nsp;
+#pragma unroll
+            for (uint32_t k = 0; k < K; k++) {
+                if ((spm >> k) & 1u) {
+                    const uint32_t p = q + (uint32_t)__popc(sb[k] & lt);
+                    S.sp[p] = x[k / SL][k % SL];
+                    S.spa[p] = nd[k / SL];
+                }
+                q += (uint32_t)__popc(sb[k]);
+            }
+            T.nsp = q;
         }
         // lists kept in the CSR: lane t takes the t-th such entry
-        const unsigned bll = __ballot_sync(kFull, is_long);
-        if (bll) {
-            unsigned mm = bll;
-            for (int q = 0; q < lane && mm; q++) mm &= mm - 1u;
-            const int src = mm ? __ffs(mm) - 1 : 0;
-            const uint32_t e2 = __shfl_sync(kFull, v, src);
-            const uint32_t a2 = __shfl_sync(kFull, aux, src);
-            expand_wave<false>(A, R, S, T, mm ? e2 : PG_NONE, a2, from_bag, lane, C);
+#pragma unroll
+        for (uint32_t u = 0; u < U; u++) {
+            const unsigned bll = __ballot_sync(kFull, is_long[u]);
+            if (bll) {
+                unsigned mm = bll;
+                for (int q = 0; q < lane && mm; q++) mm &= mm - 1u;
+                const int src = mm ? __ffs(mm) - 1 : 0;
+                const uint32_t e2 = __shfl_sync(kFull, v[u], src);
+                const uint32_t a2 = __shfl_sync(kFull, aux[u], src);
+                expand_wave<false>(A, R, S, T, mm ? e2 : PG_NONE, a2, from_bag, lane, C);
+            }
         }
     }
 }
@@ -871,12 +936,18 @@ __device__ bool cta_round(const TravArgs &A, const Round &R, const WarpSm &S, co
             T.cta_cap = QC;
             if (!kReach && A.ellw0 != 0u) {
                 // BFS reads the forward rows only: the lean level of width ellw0
-                if (A.ellw0 == 4u)
-                    bfs_rows_level<2>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C);
-                else if (A.ellw0 == 8u)
-                    bfs_rows_level<3>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C);
-                else
-                    bfs_rows_level<4>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C);
+                // one group in flight per warp when that covers the level
+                const bool one = ncur <= (uint32_t)nwib * (32u >> (A.ellw0 == 4u ? 2u : 3u));
+                if (A.ellw0 == 4u) {
+                    if (one) bfs_rows_level<2, 2, 1>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C);
+                    else bfs_rows_level<2, 2, 2>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C);
+                } else if (A.ellw0 == 8u) {
+                    if (one) bfs_rows_level<3, 3, 1>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C);
+                    else bfs_rows_level<3, 3, 2>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C);
+                } else {
+                    if (one) bfs_rows_level<4, 3, 1>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C);
+                    else bfs_rows_level<4, 3, 2>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C);
+                }
             } else if (lw) {
                 const uint32_t G = 32u >> lw;  // entries per slot-parallel wave
                 for (uint32_t w0 = (uint32_t)wib * G; w0 < ncur; w0 += (uint32_t)nwib * G)
