@@ -45,6 +45,11 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr unsigned long long kMask40 = (1ull << 40) - 1;
 constexpr uint32_t kSpillCap = 32u * kU;  // per-warp spill staging entries
 constexpr uint32_t kMaxW = 16;            // widest padded row
+// Settled-vertex filter of the CTA BFS local search: 2^kVtLog2 shared-memory
+// slots of (distance, vertex), direct-mapped; only with CTA level buffers of
+// at most kVtMaxQueue entries (so that both fit in shared memory).
+constexpr uint32_t kVtLog2 = 11;
+constexpr uint32_t kVtMaxQueue = 4096;
 
 struct TravArgs {
     PgGraphDev G;
@@ -144,6 +149,7 @@ __device__ __forceinline__ void task_init(Task &T, uint32_t budget) {
 // Shared-memory level buffers of the CTA local search.
 struct CtaSm {
     uint32_t *ent[3], *aux[3];  // three level buffers, rotating
+    unsigned long long *vt;     // settled-vertex filter (BFS), or null
     unsigned *n;                // [3] level sizes
     unsigned *task;             // grabbed task base
     unsigned *wcnt;             // [warps + 1] spill counts / offsets of a CTA flush
@@ -692,6 +698,27 @@ __device__ void expand_rows_sp(const TravArgs &A, const Round &R, const WarpSm &
     }
 }
 
+__device__ __forceinline__ uint32_t vt_slot(uint32_t v) { return (v * 0x9E3779B1u) >> (32u - kVtLog2); }
+__device__ __forceinline__ unsigned long long vt_pack(uint32_t d, uint32_t v) {
+    return ((unsigned long long)d << 32) | v;
+}
+// Filter slots are read and written by the CTA's threads concurrently, so
+// both sides are relaxed CTA-scope accesses: single-copy atomic, a reader
+// sees one whole (distance, vertex) pair, never halves of two.
+__device__ __forceinline__ unsigned long long vt_get(const unsigned long long *vt, uint32_t v) {
+    unsigned long long e;
+    asm volatile("ld.relaxed.cta.shared.u64 %0, [%1];"
+                 : "=l"(e)
+                 : "r"((unsigned)__cvta_generic_to_shared(vt + vt_slot(v))));
+    return e;
+}
+__device__ __forceinline__ void vt_put(unsigned long long *vt, uint32_t v, uint32_t d) {
+    asm volatile("st.relaxed.cta.shared.u64 [%0], %1;"
+                 :
+                 : "r"((unsigned)__cvta_generic_to_shared(vt + vt_slot(v))), "l"(vt_pack(d, v))
+                 : "memory");
+}
+
 // One level of the CTA's BFS local search over forward padded rows of width
 // W = 2^LW.  Its latency is one dependent chain per warp pass: entry (shared
 // memory), row read, atomicMin, append.  To keep the passes few, an entry
@@ -707,7 +734,8 @@ __device__ void expand_rows_sp(const TravArgs &A, const Round &R, const WarpSm &
 template <uint32_t LW, uint32_t LS, uint32_t U>
 __device__ void bfs_rows_level(const TravArgs &A, const Round &R, const WarpSm &S, Task &T,
                                const uint32_t *ents, const uint32_t *auxs, uint32_t ncur,
-                               bool from_bag, int lane, int wib, int nwib, Counters &C) {
+                               bool from_bag, int lane, int wib, int nwib, Counters &C,
+                               unsigned long long *vt) {
     constexpr uint32_t W = 1u << LW, NL = 1u << LS, SL = W >> LS, G = 32u >> LS;
     static_assert(LS <= LW && SL * U <= 8u, "at most 8 arcs per lane and pass");
     const uint32_t j = (uint32_t)lane & (NL - 1u);
@@ -733,6 +761,7 @@ __device__ void bfs_rows_level(const TravArgs &A, const Round &R, const WarpSm &
                 // a local-search entry carries its distance; a bag entry reads it
                 const uint32_t d = from_bag ? pg_ldcg(A.dist + v[u]) : aux[u];
                 nd[u] = (d == PG_INF) ? PG_INF : d + 1u;
+                if (from_bag && vt && d != PG_INF) vt_put(vt, v[u], d);
             }
         // every row read of the pass, then every atomicMin
         uint32_t x[U][SL];
@@ -746,13 +775,26 @@ __device__ void bfs_rows_level(const TravArgs &A, const Round &R, const WarpSm &
                 if (x[u][s] < 0x80000000u) x[u][s] = PG_DBG_ID(A, x[u][s], 11u, false);
 #endif
             }
+        // an arc into a vertex this CTA settled at a distance <= nd cannot
+        // improve it (distances only decrease): no atomic
+        bool go[U][SL];
+#pragma unroll
+        for (uint32_t u = 0; u < U; u++)
+#pragma unroll
+            for (uint32_t s = 0; s < SL; s++) {
+                go[u][s] = x[u][s] < 0x80000000u;  // not padding, not a CSR-row marker
+                if (vt && go[u][s]) {
+                    const unsigned long long e = vt_get(vt, x[u][s]);
+                    go[u][s] = !((uint32_t)e == x[u][s] && (uint32_t)(e >> 32) <= nd[u]);
+                }
+            }
         uint32_t old[U][SL];
 #pragma unroll
         for (uint32_t u = 0; u < U; u++)
 #pragma unroll
             for (uint32_t s = 0; s < SL; s++) {
                 old[u][s] = 0;
-                if (x[u][s] < 0x80000000u) {  // not padding, not a CSR-row marker
+                if (go[u][s]) {
                     old[u][s] = atomicMin(A.dist + x[u][s], nd[u]);
                     if (nd[u] < win) pg_prefetch_l1(ell + (size_t)x[u][s] * W);
                 }
@@ -775,6 +817,7 @@ __device__ void bfs_rows_level(const TravArgs &A, const Round &R, const WarpSm &
                 const bool arc = x[u][s] < 0x80000000u;
                 if (arc) C.exp_edges++;
                 const bool imp = arc && nd[u] < old[u][s];
+                if (imp && vt) vt_put(vt, x[u][s], nd[u]);
                 impm |= (imp ? 1u : 0u) << (u * SL + s);
                 locm |= (imp && nd[u] < win ? 1u : 0u) << (u * SL + s);
             }
@@ -939,14 +982,14 @@ __device__ bool cta_round(const TravArgs &A, const Round &R, const WarpSm &S, co
                 // one group in flight per warp when that covers the level
                 const bool one = ncur <= (uint32_t)nwib * (32u >> (A.ellw0 == 4u ? 2u : 3u));
                 if (A.ellw0 == 4u) {
-                    if (one) bfs_rows_level<2, 2, 1>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C);
-                    else bfs_rows_level<2, 2, 2>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C);
+                    if (one) bfs_rows_level<2, 2, 1>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C, Q.vt);
+                    else bfs_rows_level<2, 2, 2>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C, Q.vt);
                 } else if (A.ellw0 == 8u) {
-                    if (one) bfs_rows_level<3, 3, 1>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C);
-                    else bfs_rows_level<3, 3, 2>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C);
+                    if (one) bfs_rows_level<3, 3, 1>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C, Q.vt);
+                    else bfs_rows_level<3, 3, 2>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C, Q.vt);
                 } else {
-                    if (one) bfs_rows_level<4, 3, 1>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C);
-                    else bfs_rows_level<4, 3, 2>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C);
+                    if (one) bfs_rows_level<4, 3, 1>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C, Q.vt);
+                    else bfs_rows_level<4, 3, 2>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C, Q.vt);
                 }
             } else if (lw) {
                 const uint32_t G = 32u >> lw;  // entries per slot-parallel wave
@@ -1185,6 +1228,11 @@ __device__ __forceinline__ float flog2p1(float x) { return log2f(1.0f + x); }
 // not evaluated outside that range.
 constexpr uint32_t kRoundFeatureCap = 1u << 14;
 
+// Whether the settled-vertex filter has room beside the CTA level buffers.
+__host__ __device__ __forceinline__ bool vt_enabled(const PgLaunch &L) {
+    return L.vgc != PG_VGC_WARP && L.cta_queue <= kVtMaxQueue;
+}
+
 // Per-warp FIFO words (entry + aux per slot): only the warp local search
 // uses the FIFO, so the CTA local search leaves it out of shared memory.
 __host__ __device__ __forceinline__ uint32_t warp_fifo_words(const PgLaunch &L) {
@@ -1229,6 +1277,12 @@ __global__ void __launch_bounds__(512, 1) pg_traverse_kernel(const TravArgs A) {
         }
         Q.n = cta + 6u * A.L.cta_queue;
         Q.task = Q.n + 3;
+        // the filter follows the level buffers (8-byte aligned: every region
+        // before it is a multiple of 8 bytes)
+        Q.vt = (!kReach && A.ellw0 != 0u && vt_enabled(A.L))
+                   ? reinterpret_cast<unsigned long long *>(Q.n + 4) : nullptr;
+        if (Q.vt)
+            for (uint32_t i = threadIdx.x; i < (1u << kVtLog2); i += blockDim.x) Q.vt[i] = ~0ull;
     }
     __shared__ unsigned s_wcnt[17];
     Q.wcnt = s_wcnt;
@@ -1558,7 +1612,7 @@ size_t traverse_smem(const PgLaunch &L) {
     const uint32_t nw = L.threads / 32;
     return 6144 + (size_t)nw * 256 +
            (size_t)nw * (4u * 32u + 2u * kSpillCap + 2u * warp_fifo_words(L)) * 4u +
-           (size_t)(6u * L.cta_queue + 4u) * 4u;
+           (size_t)(6u * L.cta_queue + 4u) * 4u + (vt_enabled(L) ? (8u << kVtLog2) : 0u);
 }
 
 template <bool kReach>
