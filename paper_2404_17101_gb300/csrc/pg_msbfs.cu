@@ -45,8 +45,11 @@ namespace {
 constexpr uint32_t kHeavy = 32;    // edges: below, one thread (bottom-up) / one lane (top-down)
 constexpr uint32_t kChunkDefault = 1024;  // edges per chunk of a heavy vertex
 constexpr uint32_t kGather = 8;    // bottom-up: in-neighbour gathers in flight per light vertex
+constexpr uint32_t kGatherSparse = 4;  // the same in a sparse round (bitmap word, then visit word)
+constexpr uint32_t kChunkSteps = 4;  // bottom-up chunk pass: 32-edge steps per lane in flight
 constexpr uint32_t kPlanes = 5;    // distance bit-planes: distances 0..30, code 31 = written directly
 constexpr uint32_t kDirect = (1u << kPlanes) - 1u;
+constexpr uint32_t kSparse = 32;   // bottom-up round with |F| < n / kSparse: frontier bitmap filter
 }  // namespace
 
 // Per-round list sizes; round r reads slot r % 4 and fills slot (r + 1) % 4.
@@ -64,6 +67,7 @@ struct PgMsbfsWork {
     unsigned long long *planes;  // [kPlanes][n]
     uint32_t *front[2], *unfin[2], *touched;
     uint32_t *flev;              // round whose frontier a vertex last joined (its visit word's age)
+    uint32_t *fbits;             // frontier bitmap of a sparse bottom-up round, ceil(n / 32) words
     MsCount *cnt;                // [4]
     uint32_t n;
     uint2 *chunks[2];            // (vertex, first edge) per chunk: out-lists, in-lists
@@ -76,6 +80,7 @@ void pg_msbfs_release(pg_graph *g) {
         cudaFree(g->msbfs->seen);
         cudaFree(g->msbfs->front[0]);
         cudaFree(g->msbfs->cnt);
+        cudaFree(g->msbfs->fbits);
         cudaFree(g->msbfs->chunks[0]);
         if (g->msbfs->chunks[1] != g->msbfs->chunks[0]) cudaFree(g->msbfs->chunks[1]);
         delete g->msbfs;
@@ -120,6 +125,7 @@ struct MsArgs {
     unsigned long long *seen, *visit0, *visit1, *next, *planes;
     uint32_t *front0, *front1, *unfin0, *unfin1, *touched;
     uint32_t *flev;
+    uint32_t *fbits;      // ceil(n / 32) words, all zero between rounds
     uint32_t *dist;       // k * n, source-major
     uint32_t k;
     uint32_t sources[64];
@@ -191,6 +197,8 @@ __global__ void __launch_bounds__(512) pg_msbfs_kernel(const MsArgs A) {
         A.flev[v] = 0;
         for (uint32_t p = 0; p < kPlanes; p++) A.planes[(size_t)p * n + v] = 0;
     }
+    const uint32_t nw = (n + 31u) >> 5;  // frontier bitmap words
+    for (uint32_t i = gtid; i < nw; i += gthreads) A.fbits[i] = 0;
 
     if (gtid == 0) {
         // the first frontier: the distinct sources
@@ -214,6 +222,7 @@ __global__ void __launch_bounds__(512) pg_msbfs_kernel(const MsArgs A) {
     const unsigned long long t_deadline = pg_gtimer() + 16ull * A.timeout_ns;
     bool bottom_up = false;
     bool uall = true;          // no bottom-up round yet: every vertex is unfinished
+    bool fdirty = false;       // the bitmap holds the last sparse round's frontier
     uint32_t up = 0, Ucur = 0; // current unfinished list and its size
     uint32_t L = 0, pulls = 0;
     for (;; L++) {
@@ -253,47 +262,86 @@ __global__ void __launch_bounds__(512) pg_msbfs_kernel(const MsArgs A) {
         uint32_t *front_nxt = cur ? A.front0 : A.front1;
         const uint32_t dnew = L + 1u;
         unsigned long long ne = 0;  // out-degree sum of the next frontier
+        // A sparse bottom-up round marks its frontier in a bitmap (n / 8
+        // bytes, resident in L2), and a gather reads an in-neighbour's visit
+        // word only when its bit is set: the other words hold no bit of this
+        // round.  The bitmap is cleared in the round after its use.
+        const bool sparse = bottom_up && (unsigned long long)F * kSparse < (unsigned long long)n;
+        const bool cleared = fdirty;
+        if (fdirty) {
+            for (uint32_t i = gtid; i < nw; i += gthreads) A.fbits[i] = 0;
+            fdirty = false;
+        }
+        if (sparse) {
+            if (cleared && !pg_grid_sync(ctrl, gridDim.x, gen, A.timeout_ns, &s_flag)) break;
+            for (uint32_t i = gtid; i < F; i += gthreads) {
+                const uint32_t v = __ldcg(front_cur + i);
+                atomicOr(A.fbits + (v >> 5), 1u << (v & 31u));
+            }
+            if (!pg_grid_sync(ctrl, gridDim.x, gen, A.timeout_ns, &s_flag)) break;
+            fdirty = true;
+        }
         if (bottom_up) {
             pulls++;
             const uint32_t *ulist = up ? A.unfin1 : A.unfin0;
             uint32_t *unext = up ? A.unfin0 : A.unfin1;
             const uint32_t U = uall ? n : Ucur;
-            // light vertices: one thread each, kGather gathers in flight;
-            // warps take consecutive list positions (whole-warp appends)
+            // light vertices: one thread each, kGather gathers in flight,
+            // stopping at the first step that completes the vertex; warps
+            // take consecutive list positions (whole-warp appends)
             for (uint32_t b0 = gwarp * 32u; b0 < U; b0 += nwarps * 32u) {
                 const uint32_t i = b0 + (uint32_t)lane;
-                uint32_t w = PG_NONE;
+                uint32_t w = PG_NONE, b = 0, e = 0;
                 if (i < U) w = uall ? i : __ldcg(ulist + i);
-                unsigned long long s = 0, nb = 0;
+                unsigned long long s = 0, need = 0, acc = 0, nb = 0;
                 bool keep = false, light = false;
                 if (w != PG_NONE) {
                     s = A.seen[w];
-                    const unsigned long long need = full & ~s;
+                    need = full & ~s;
                     if (need) {
-                        const uint32_t b = __ldg(A.G.toff + w), e = __ldg(A.G.toff + w + 1);
-                        if (e - b < kHeavy) {
-                            light = true;
-                            unsigned long long acc = 0;
-                            for (uint32_t q = b; q < e; q += kGather) {
-                                uint32_t u[kGather];
-#pragma unroll
-                                for (int t = 0; t < (int)kGather; t++)
-                                    u[t] = (q + t < e) ? __ldg(A.G.tidx + q + t) : PG_NONE;
-#pragma unroll
-                                for (int t = 0; t < (int)kGather; t++)
-                                    if (u[t] != PG_NONE) acc |= __ldcg(visit_cur + u[t]);
-                                if ((acc & need) == need) break;
-                            }
-                            nb = acc & need;
-                            if (nb) {
-                                A.seen[w] = s | nb;
-                                record_bits(A, visit_nxt, w, nb, dnew);
-                                ne += __ldg(A.G.off + w + 1) - __ldg(A.G.off + w);
-                            }
-                            keep = nb != need && e > b;  // still missing bits, reachable
-                        }
+                        b = __ldg(A.G.toff + w);
+                        e = __ldg(A.G.toff + w + 1);
                         // heavy vertices are updated (and listed) by the chunk pass
+                        light = e - b < kHeavy;
                     }
+                }
+                if (light) {
+                    if (sparse) {
+                        // bitmap first: a visit word only for a frontier neighbour
+                        for (uint32_t q = b; q < e; q += kGatherSparse) {
+                            uint32_t u[kGatherSparse], bw[kGatherSparse];
+#pragma unroll
+                            for (int t = 0; t < (int)kGatherSparse; t++)
+                                u[t] = (q + t < e) ? __ldg(A.G.tidx + q + t) : PG_NONE;
+#pragma unroll
+                            for (int t = 0; t < (int)kGatherSparse; t++)
+                                bw[t] = (u[t] != PG_NONE) ? __ldcg(A.fbits + (u[t] >> 5)) : 0u;
+#pragma unroll
+                            for (int t = 0; t < (int)kGatherSparse; t++)
+                                if ((bw[t] >> (u[t] & 31u)) & 1u) acc |= __ldcg(visit_cur + u[t]);
+                            if ((acc & need) == need) break;
+                        }
+                    } else {
+                        for (uint32_t q = b; q < e; q += kGather) {
+                            uint32_t u[kGather];
+#pragma unroll
+                            for (int t = 0; t < (int)kGather; t++)
+                                u[t] = (q + t < e) ? __ldg(A.G.tidx + q + t) : PG_NONE;
+#pragma unroll
+                            for (int t = 0; t < (int)kGather; t++)
+                                if (u[t] != PG_NONE) acc |= __ldcg(visit_cur + u[t]);
+                            if ((acc & need) == need) break;
+                        }
+                    }
+                }
+                if (light) {
+                    nb = acc & need;
+                    if (nb) {
+                        A.seen[w] = s | nb;
+                        record_bits(A, visit_nxt, w, nb, dnew);
+                        ne += __ldg(A.G.off + w + 1) - __ldg(A.G.off + w);
+                    }
+                    keep = nb != need && e > b;  // still missing bits, reachable
                 }
                 list_append(front_nxt, &cn->F, light && nb != 0, w, lane);
                 list_append(unext, &cn->U, keep, w, lane);
@@ -305,9 +353,25 @@ __global__ void __launch_bounds__(512) pg_msbfs_kernel(const MsArgs A) {
                 const unsigned long long need = full & ~__ldcg(A.seen + w);
                 if (!need) continue;
                 const uint32_t e = min(ch.y + A.clen, __ldg(A.G.toff + w + 1));
+                // kChunkSteps steps of 32 edges per pass: every index read of
+                // the pass, then every gather, one warp OR per pass
                 unsigned long long acc = 0;
-                for (uint32_t q = ch.y; q < e; q += 32u) {
-                    if (q + lane < e) acc |= __ldcg(visit_cur + __ldg(A.G.tidx + q + lane));
+                for (uint32_t q0 = ch.y; q0 < e; q0 += 32u * kChunkSteps) {
+                    uint32_t u[kChunkSteps];
+#pragma unroll
+                    for (int t = 0; t < (int)kChunkSteps; t++) {
+                        const uint32_t q = q0 + 32u * (uint32_t)t + (uint32_t)lane;
+                        u[t] = (q < e) ? __ldg(A.G.tidx + q) : PG_NONE;
+                    }
+                    if (sparse) {
+#pragma unroll
+                        for (int t = 0; t < (int)kChunkSteps; t++)
+                            if (u[t] != PG_NONE && !((__ldcg(A.fbits + (u[t] >> 5)) >> (u[t] & 31u)) & 1u))
+                                u[t] = PG_NONE;
+                    }
+#pragma unroll
+                    for (int t = 0; t < (int)kChunkSteps; t++)
+                        if (u[t] != PG_NONE) acc |= __ldcg(visit_cur + u[t]);
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) acc |= __shfl_xor_sync(kFull, acc, o);
                     if ((acc & need) == need) break;
@@ -514,9 +578,11 @@ pg_status pg_launch_msbfs(pg_graph *g, PgLaunch &L, const uint32_t *sources, uin
         cudaError_t e = cudaMalloc(&p, (4 + kPlanes) * n * sizeof(unsigned long long));
         if (e == cudaSuccess) e = cudaMalloc(&q, 6 * n * sizeof(uint32_t));
         if (e == cudaSuccess) e = cudaMalloc(&W->cnt, 4 * sizeof(MsCount));
+        if (e == cudaSuccess) e = cudaMalloc(&W->fbits, ((n + 31) / 32) * sizeof(uint32_t));
         if (e != cudaSuccess) {
             cudaFree(p);
             cudaFree(q);
+            cudaFree(W->cnt);
             delete W;
             return pg_cuda_error(e, "cudaMalloc(batched BFS words)");
         }
@@ -576,6 +642,7 @@ pg_status pg_launch_msbfs(pg_graph *g, PgLaunch &L, const uint32_t *sources, uin
     A.unfin1 = W.unfin[1];
     A.touched = W.touched;
     A.flev = W.flev;
+    A.fbits = W.fbits;
     A.dist = dist;
     A.k = k;
     for (uint32_t j = 0; j < k; j++) A.sources[j] = sources[j];
