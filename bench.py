@@ -226,6 +226,14 @@ def latency_floor(pg, gg, rounds, levels, kernel_ms):
                    "barriers, per level"}
 
 
+def learned_on(pg, cfg):
+    """The learned per-round schedule on top of `cfg`: same launch shape, and
+    cfg's tau is the fixed action the network falls back to."""
+    c = pg.Config.from_buffer_copy(cfg)
+    c.schedule = pg.PG_SCHED_LEARNED
+    return c
+
+
 def other_configs(pg, gg, peak, steps, warm, with_oracle):
     """Timed forms of the other benchmark configurations (one GPU):
     C3 (R-MAT 24, 64 single-source BFS vs one 64-source batch), C4 (directed
@@ -382,14 +390,17 @@ def other_configs(pg, gg, peak, steps, warm, with_oracle):
     del G, dsp, wts
     torch.cuda.empty_cache()
 
-    # ---- C1 and C5 held-out kNN: plain tau 16, tau 64, learned
+    # ---- C1 and C5 held-out kNN: fixed tau 16 / 32 / 64, the autotuned
+    # configuration, and the learned schedule on top of it
     for name, make in (("C1 grid_1000", gg.grid_1000), ("C5 knn_30m_k3", gg.knn_30m_k3)):
         g = make()
         G = pg.Graph.from_graphgen(g, ell=True)
-        forms = {"plain_tau16": pg.default_config(), "plain_tau64": pg.default_config(tau=64)}
+        forms = {"plain_tau16": pg.default_config(), "plain_tau32": pg.default_config(tau=32),
+                 "plain_tau64": pg.default_config(tau=64),
+                 "plain_tuned": G.autotune([0], kind=0, trials=1, cfg=pg.default_config())}
         if w is not None:
             G.set_schedule_weights(w)
-            forms["learned"] = pg.default_config(schedule=pg.PG_SCHED_LEARNED)
+            forms["learned"] = learned_on(pg, forms["plain_tuned"])
         outs, fr = {}, {}
         for f_, cfg in forms.items():
             o = torch.empty(g.n, dtype=torch.int32, device="cuda")
@@ -496,10 +507,13 @@ def run_configs(args):
     def bfs_forms(name, g, extra=None):
         G = pg.Graph.from_graphgen(g, ell=True)
         out = torch.empty(g.n, dtype=torch.int32, device="cuda")
-        forms = {"tau16": pg.default_config(), "tau64": pg.default_config(tau=64)}
+        forms = {"tau16": pg.default_config(), "tau32": pg.default_config(tau=32),
+                 "tau64": pg.default_config(tau=64)}
+        if not name.startswith("strip"):
+            forms["tuned"] = G.autotune([0], kind=0, trials=1, cfg=pg.default_config())
         if w is not None:
             G.set_schedule_weights(w)
-            forms["learned"] = pg.default_config(schedule=pg.PG_SCHED_LEARNED)
+            forms["learned"] = learned_on(pg, forms.get("tuned", forms["tau64"]))
         if extra:
             forms.update(extra)
         res, ref = {}, None
@@ -614,7 +628,8 @@ def main():
 
     # --- forms: the plain fixed-tau traversal (library defaults), the same
     # with tau and launch shape picked by the autotuner for this graph, and
-    # the learned per-round schedule (when trained weights exist)
+    # the learned per-round schedule (when trained weights exist) on top of
+    # the tuned configuration: the network's fallback action is the tuned tau
     plain_cfg = pg.default_config()
     forms = {"plain": plain_cfg}
     tuned = None
@@ -625,7 +640,7 @@ def main():
     w = pg.trained_weights()
     if w is not None:
         G.set_schedule_weights(w)
-        forms["learned"] = pg.default_config(schedule=pg.PG_SCHED_LEARNED)
+        forms["learned"] = learned_on(pg, forms.get("plain_tuned", plain_cfg))
 
     G.bfs(src, out=out, cfg=plain_cfg)
     n_r, m_r = G.count_reached(out)

@@ -288,7 +288,9 @@ __global__ void __launch_bounds__(512) pg_msbfs_kernel(const MsArgs A) {
             const uint32_t U = uall ? n : Ucur;
             // light vertices: one thread each, kGather gathers in flight,
             // stopping at the first step that completes the vertex; warps
-            // take consecutive list positions (whole-warp appends)
+            // take consecutive list positions (whole-warp appends).  The
+            // in-list indices are read once per round: streaming loads keep
+            // them from displacing the visit words in L2.
             for (uint32_t b0 = gwarp * 32u; b0 < U; b0 += nwarps * 32u) {
                 const uint32_t i = b0 + (uint32_t)lane;
                 uint32_t w = PG_NONE, b = 0, e = 0;
@@ -312,7 +314,7 @@ __global__ void __launch_bounds__(512) pg_msbfs_kernel(const MsArgs A) {
                             uint32_t u[kGatherSparse], bw[kGatherSparse];
 #pragma unroll
                             for (int t = 0; t < (int)kGatherSparse; t++)
-                                u[t] = (q + t < e) ? __ldg(A.G.tidx + q + t) : PG_NONE;
+                                u[t] = (q + t < e) ? __ldcs(A.G.tidx + q + t) : PG_NONE;
 #pragma unroll
                             for (int t = 0; t < (int)kGatherSparse; t++)
                                 bw[t] = (u[t] != PG_NONE) ? __ldcg(A.fbits + (u[t] >> 5)) : 0u;
@@ -326,7 +328,7 @@ __global__ void __launch_bounds__(512) pg_msbfs_kernel(const MsArgs A) {
                             uint32_t u[kGather];
 #pragma unroll
                             for (int t = 0; t < (int)kGather; t++)
-                                u[t] = (q + t < e) ? __ldg(A.G.tidx + q + t) : PG_NONE;
+                                u[t] = (q + t < e) ? __ldcs(A.G.tidx + q + t) : PG_NONE;
 #pragma unroll
                             for (int t = 0; t < (int)kGather; t++)
                                 if (u[t] != PG_NONE) acc |= __ldcg(visit_cur + u[t]);
@@ -361,7 +363,7 @@ __global__ void __launch_bounds__(512) pg_msbfs_kernel(const MsArgs A) {
 #pragma unroll
                     for (int t = 0; t < (int)kChunkSteps; t++) {
                         const uint32_t q = q0 + 32u * (uint32_t)t + (uint32_t)lane;
-                        u[t] = (q < e) ? __ldg(A.G.tidx + q) : PG_NONE;
+                        u[t] = (q < e) ? __ldcs(A.G.tidx + q) : PG_NONE;
                     }
                     if (sparse) {
 #pragma unroll
