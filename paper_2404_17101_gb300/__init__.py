@@ -245,6 +245,9 @@ class Graph:
         src = np.ascontiguousarray(sources, dtype=np.uint32)
         if out is None:
             out = torch.empty((len(src), self.n), dtype=torch.int32, device="cuda")
+        elif not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.int32
+                  and out.is_contiguous() and out.numel() >= len(src) * self.n):
+            raise ValueError("out must be a contiguous CUDA int32 tensor of k * n elements")
         _check(load().pg_bfs_multi(self._h, ctypes.c_void_p(src.ctypes.data), len(src),
                                    ctypes.c_void_p(out.data_ptr()),
                                    ctypes.byref(cfg) if cfg else None,

@@ -86,6 +86,28 @@ def test_bfs_multi_vs_oracle(pg, make, k):
         assert np.array_equal(D, want), direction
 
 
+def test_bfs_multi_output_alignment(pg):
+    """The decode pass writes four vertices per 16-byte store when n is a
+    multiple of 4 and the output starts on a 16-byte boundary, else one per
+    4-byte store: an output 4 bytes past an aligned start takes the second
+    path; distances up to ~100 exercise the directly written codes (>= 31);
+    a short output is refused before anything launches."""
+    import torch
+    g = gg.knn(20_000, 5, 3)
+    assert g.n % 4 == 0
+    G = pg.Graph.from_graphgen(g)
+    srcs = gg.pick_sources(g, 9, 2)
+    want = oracle.bfs_multi(g, srcs)
+    assert want[want != oracle.INF].max() >= 31
+    buf = torch.empty(9 * g.n + 4, dtype=torch.int32, device="cuda")
+    for off in (0, 1):
+        D = buf[off:off + 9 * g.n].view(9, g.n)
+        G.bfs_multi(srcs, out=D)
+        assert np.array_equal(pg.to_uint32(D), want), off
+    with pytest.raises(ValueError):
+        G.bfs_multi(srcs, out=buf[:9 * g.n - 1])
+
+
 def test_bfs_multi_duplicate_sources(pg):
     g = gg.knn(5000, 4, 1)
     G = pg.Graph.from_graphgen(g)
