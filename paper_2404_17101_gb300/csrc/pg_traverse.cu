@@ -698,6 +698,89 @@ __device__ void expand_rows_sp(const TravArgs &A, const Round &R, const WarpSm &
     }
 }
 
+// One level of the CTA's reachability search over padded rows: the
+// slot-parallel wave of expand_rows_sp (lane l takes entry l / W and slot
+// l % W, W = the widest row of the two directions), with U groups of
+// 32 / W entries per warp in flight: every mask and row read of the pass is
+// issued before the first atomicOr, and every atomicOr before the first
+// result is used.  Entries whose list is in the CSR (long rows, or a
+// direction without rows) are expanded afterwards, one per lane, by
+// expand_wave.
+template <uint32_t LW, uint32_t U>
+__device__ void reach_rows_level(const TravArgs &A, const Round &R, const WarpSm &S, Task &T,
+                                 const uint32_t *ents, const uint32_t *auxs, uint32_t ncur,
+                                 bool from_bag, int lane, int wib, int nwib, Counters &C) {
+    constexpr uint32_t W = 1u << LW, G = 32u >> LW;
+    const uint32_t j = (uint32_t)lane & (W - 1u);
+    const uint32_t gstride = (uint32_t)nwib * G;
+    for (uint32_t w0 = (uint32_t)wib * G; w0 < ncur; w0 += gstride * U) {
+        uint32_t ent[U], aux[U], x[U];
+        unsigned long long prop[U], old[U];
+#pragma unroll
+        for (uint32_t u = 0; u < U; u++) {
+            const uint32_t i = w0 + u * gstride + ((uint32_t)lane >> LW);
+            ent[u] = PG_NONE;
+            aux[u] = 0;
+            if (i < ncur) {
+                ent[u] = PG_DBG_ENTRY(A, ents[i], 8u, true);
+                aux[u] = auxs[i];
+            }
+        }
+        // every mask and row read of the pass
+#pragma unroll
+        for (uint32_t u = 0; u < U; u++) {
+            prop[u] = 0;
+            x[u] = PG_NONE;
+            if (ent[u] != PG_NONE) {
+                const uint32_t v = ent[u] & 0x7FFFFFFFu, dir = ent[u] >> 31;
+                const uint32_t *ell = dir ? A.ell1 : A.ell0;
+                const uint32_t Wd = dir ? A.ellw1 : A.ellw0;
+                prop[u] = load_prop<true>(A, v, dir);
+                if (ell != nullptr && j < Wd) x[u] = __ldg(ell + (size_t)v * Wd + j);
+#ifdef PG_DEBUG_BOUNDS
+                if (x[u] < 0x80000000u) x[u] = PG_DBG_ID(A, x[u], 9u, false);
+#endif
+            }
+        }
+        // every atomicOr of the pass
+#pragma unroll
+        for (uint32_t u = 0; u < U; u++) {
+            const bool arc = ent[u] != PG_NONE && x[u] < 0x80000000u;
+            const uint32_t dir = ent[u] >> 31;
+            old[u] = relax_issue<true>(A, x[u], dir, prop[u], arc);
+            if (arc && aux[u] + 1u < R.tau) {
+                const uint32_t *ell = dir ? A.ell1 : A.ell0;
+                const uint32_t Wd = dir ? A.ellw1 : A.ellw0;
+                pg_prefetch_l1(ell + (size_t)x[u] * Wd);
+            }
+        }
+        // stage the improved children, then the lists kept in the CSR
+#pragma unroll
+        for (uint32_t u = 0; u < U; u++) {
+            const bool live = ent[u] != PG_NONE;
+            const uint32_t dir = ent[u] >> 31;
+            const bool has_rows = live && (dir ? A.ell1 : A.ell0) != nullptr;
+            const bool lead = live && j == 0u;
+            const bool is_long = lead && (!has_rows || x[u] == PG_ELL_LONG);
+            const uint32_t caux = aux[u] + 1u;
+            const bool arc = live && x[u] < 0x80000000u;
+            const bool imp = arc && improved<true>(prop[u], old[u]);
+            if (lead && !is_long) { C.expansions++; C.exp_verts++; }
+            if (arc) C.exp_edges++;
+            stage<true>(A, R, S, T, imp, x[u] | (dir << 31), caux, eligible<true>(R, caux), lane, C);
+            const unsigned bl = __ballot_sync(kFull, is_long);
+            if (bl) {
+                unsigned mm = bl;
+                for (int q = 0; q < lane && mm; q++) mm &= mm - 1u;
+                const int src = mm ? __ffs(mm) - 1 : 0;
+                const uint32_t e2 = __shfl_sync(kFull, ent[u], src);
+                const uint32_t a2 = __shfl_sync(kFull, aux[u], src);
+                expand_wave<true>(A, R, S, T, mm ? e2 : PG_NONE, a2, from_bag, lane, C);
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ uint32_t vt_slot(uint32_t v) { return (v * 0x9E3779B1u) >> (32u - kVtLog2); }
 __device__ __forceinline__ unsigned long long vt_pack(uint32_t d, uint32_t v) {
     return ((unsigned long long)d << 32) | v;
@@ -991,6 +1074,14 @@ __device__ bool cta_round(const TravArgs &A, const Round &R, const WarpSm &S, co
                     if (one) bfs_rows_level<4, 3, 1>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C, Q.vt);
                     else bfs_rows_level<4, 3, 2>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C, Q.vt);
                 }
+            } else if (kReach && lw) {
+                // reachability: two entry groups in flight per warp
+                if (lw == 2u)
+                    reach_rows_level<2, 2>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C);
+                else if (lw == 3u)
+                    reach_rows_level<3, 2>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C);
+                else
+                    reach_rows_level<4, 2>(A, R, S, T, Q.ent[cl], Q.aux[cl], ncur, h == 0, lane, wib, nwib, C);
             } else if (lw) {
                 const uint32_t G = 32u >> lw;  // entries per slot-parallel wave
                 for (uint32_t w0 = (uint32_t)wib * G; w0 < ncur; w0 += (uint32_t)nwib * G)
