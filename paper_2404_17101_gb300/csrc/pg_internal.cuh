@@ -236,6 +236,12 @@ pg_status pg_launch_traverse(pg_graph *g, PgLaunch &L, int kind, uint32_t src,
                              const uint32_t *sources, uint32_t k, uint32_t dir,
                              uint32_t *dist, unsigned long long *fwd, unsigned long long *bwd,
                              cudaStream_t s);
+// kind != 0 of pg_launch_traverse (reachability), defined in its own
+// translation unit (pg_traverse_reach.cu)
+pg_status pg_launch_traverse_reach(pg_graph *g, PgLaunch &L, int kind, uint32_t src,
+                                   const uint32_t *sources, uint32_t k, uint32_t dir,
+                                   uint32_t *dist, unsigned long long *fwd,
+                                   unsigned long long *bwd, cudaStream_t s);
 pg_status pg_launch_msbfs(pg_graph *g, PgLaunch &L, const uint32_t *sources, uint32_t k,
                           uint32_t chunk_len, uint32_t *dist, cudaStream_t s);
 

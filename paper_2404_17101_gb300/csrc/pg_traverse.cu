@@ -1736,7 +1736,47 @@ pg_status launch_impl(pg_graph *g, PgLaunch &L, TravArgs &A, cudaStream_t s) {
     return PG_OK;
 }
 
+void fill_traverse_args(TravArgs &A, const pg_graph *g, const PgLaunch &L, int kind,
+                        uint32_t src, const uint32_t *sources, uint32_t k, uint32_t dir,
+                        uint32_t *dist, unsigned long long *fwd, unsigned long long *bwd) {
+    memset(&A, 0, sizeof(A));
+    A.G.off = g->d_off;
+    A.G.idx = g->d_idx;
+    A.G.toff = g->d_toff ? g->d_toff : g->d_off;
+    A.G.tidx = g->d_tidx ? g->d_tidx : g->d_idx;
+    A.G.n = g->n;
+    A.G.m = g->m;
+    A.ell0 = g->d_ell[0];
+    A.ellw0 = g->d_ell[0] ? g->ellw[0] : 0u;
+    A.ell1 = g->d_ell[1];
+    A.ellw1 = g->d_ell[1] ? g->ellw[1] : 0u;
+    A.ctrl = g->d_ctrl;
+    A.bag = g->d_bag;
+    A.cap = g->bag_cap;
+    A.stamp = g->d_stamp;
+    A.hubs = g->d_hubs;
+    A.hcap = g->hub_cap;
+    A.dist = dist;
+    A.mask0 = fwd;
+    A.mask1 = bwd;
+    A.src = src;
+    A.k = k;
+    A.dir = dir;
+    A.need_deg = (kind == 0 && L.schedule == PG_SCHED_FIXED && L.direction == PG_DIR_AUTO &&
+                  L.allow_pull) ? 1u : 0u;
+    const uint32_t md =
+        (kind == 1 && (dir & PG_BWD)) ? max(g->maxdeg[0], g->maxdeg[1]) : g->maxdeg[0];
+    A.hubs_possible = md >= L.hub_degree ? 1u : 0u;
+    for (uint32_t j = 0; j < k && j < 64; j++) A.sources[j] = sources[j];
+}
+
 }  // namespace
+
+// The two instantiations of the kernel are compiled in separate translation
+// units (this file for BFS, pg_traverse_reach.cu for reachability, which
+// includes it with PG_TRAVERSE_REACH_TU defined), so that they build in
+// parallel; each unit emits device code only for the kernel it launches.
+#ifndef PG_TRAVERSE_REACH_TU
 
 pg_status pg_launch_bfs_raw(const PgRawBfs &w, PgLaunch &L, cudaStream_t s) {
     TravArgs A;
@@ -1784,36 +1824,21 @@ pg_status pg_launch_bfs_raw(const PgRawBfs &w, PgLaunch &L, cudaStream_t s) {
 pg_status pg_launch_traverse(pg_graph *g, PgLaunch &L, int kind, uint32_t src,
                              const uint32_t *sources, uint32_t k, uint32_t dir, uint32_t *dist,
                              unsigned long long *fwd, unsigned long long *bwd, cudaStream_t s) {
+    if (kind != 0) return pg_launch_traverse_reach(g, L, kind, src, sources, k, dir, dist, fwd, bwd, s);
     TravArgs A;
-    memset(&A, 0, sizeof(A));
-    A.G.off = g->d_off;
-    A.G.idx = g->d_idx;
-    A.G.toff = g->d_toff ? g->d_toff : g->d_off;
-    A.G.tidx = g->d_tidx ? g->d_tidx : g->d_idx;
-    A.G.n = g->n;
-    A.G.m = g->m;
-    A.ell0 = g->d_ell[0];
-    A.ellw0 = g->d_ell[0] ? g->ellw[0] : 0u;
-    A.ell1 = g->d_ell[1];
-    A.ellw1 = g->d_ell[1] ? g->ellw[1] : 0u;
-    A.ctrl = g->d_ctrl;
-    A.bag = g->d_bag;
-    A.cap = g->bag_cap;
-    A.stamp = g->d_stamp;
-    A.hubs = g->d_hubs;
-    A.hcap = g->hub_cap;
-    A.dist = dist;
-    A.mask0 = fwd;
-    A.mask1 = bwd;
-    A.src = src;
-    A.k = k;
-    A.dir = dir;
-    A.need_deg = (kind == 0 && L.schedule == PG_SCHED_FIXED && L.direction == PG_DIR_AUTO &&
-                  L.allow_pull) ? 1u : 0u;
-    const uint32_t md =
-        (kind == 1 && (dir & PG_BWD)) ? max(g->maxdeg[0], g->maxdeg[1]) : g->maxdeg[0];
-    A.hubs_possible = md >= L.hub_degree ? 1u : 0u;
-    for (uint32_t j = 0; j < k && j < 64; j++) A.sources[j] = sources[j];
-    if (kind == 0) return launch_impl<false>(g, L, A, s);
+    fill_traverse_args(A, g, L, kind, src, sources, k, dir, dist, fwd, bwd);
+    return launch_impl<false>(g, L, A, s);
+}
+
+#else
+
+pg_status pg_launch_traverse_reach(pg_graph *g, PgLaunch &L, int kind, uint32_t src,
+                                   const uint32_t *sources, uint32_t k, uint32_t dir,
+                                   uint32_t *dist, unsigned long long *fwd,
+                                   unsigned long long *bwd, cudaStream_t s) {
+    TravArgs A;
+    fill_traverse_args(A, g, L, kind, src, sources, k, dir, dist, fwd, bwd);
     return launch_impl<true>(g, L, A, s);
 }
+
+#endif  // PG_TRAVERSE_REACH_TU
