@@ -159,12 +159,66 @@ def _u32_array(x):
     return ctypes.c_void_p(a.ctypes.data), a
 
 
-class Graph:
-    """A graph resident on the current CUDA device."""
+def _buf(t, count, what, torch_dtypes, np_dtype, device=None, cuda_only=False, writes=True):
+    """Pointer to a caller-given buffer of at least `count` elements.
 
-    def __init__(self, handle, n, m, directed):
+    The C ABI sees raw pointers and no sizes, so a short, strided or
+    wrongly typed buffer would be read or written past its end by a kernel.
+    Checked here, before anything is launched (ValueError): the element
+    type, contiguity, size, and for a CUDA tensor the device the graph
+    lives on (`device`; None skips the check).  Host buffers (numpy arrays,
+    CPU tensors) are staged and copied by the library unless `cuda_only`."""
+    import torch
+    if isinstance(t, torch.Tensor):
+        if t.dtype not in torch_dtypes:
+            raise ValueError(f"{what}: dtype {t.dtype}, expected {' or '.join(map(str, torch_dtypes))}")
+        if not t.is_contiguous():
+            raise ValueError(f"{what}: tensor must be contiguous")
+        if t.numel() < count:
+            raise ValueError(f"{what}: {t.numel()} elements, fewer than the {count} needed")
+        if cuda_only and not t.is_cuda:
+            raise ValueError(f"{what}: must be a CUDA tensor")
+        if t.is_cuda and device is not None and t.device.index != device:
+            raise ValueError(f"{what}: tensor on cuda:{t.device.index}, the graph is on cuda:{device}")
+        return ctypes.c_void_p(t.data_ptr())
+    if isinstance(t, np.ndarray) and not cuda_only:
+        if t.dtype != np_dtype:
+            raise ValueError(f"{what}: dtype {t.dtype}, expected {np.dtype(np_dtype)}")
+        if not t.flags.c_contiguous or (writes and not t.flags.writeable):
+            raise ValueError(f"{what}: array must be C-contiguous" + (" and writeable" if writes else ""))
+        if t.size < count:
+            raise ValueError(f"{what}: {t.size} elements, fewer than the {count} needed")
+        return ctypes.c_void_p(t.ctypes.data)
+    raise ValueError(f"{what}: expected a {'CUDA tensor' if cuda_only else 'torch tensor or numpy array'}, "
+                     f"got {type(t).__name__}")
+
+
+def _u32_types():
+    import torch
+    return (torch.int32, torch.uint32)
+
+
+def _u64_types():
+    import torch
+    return (torch.int64, torch.uint64)
+
+
+def _f32_types():
+    import torch
+    return (torch.float32,)
+
+
+class Graph:
+    """A graph resident on the CUDA device that was current at upload."""
+
+    def __init__(self, handle, n, m, directed, device=None):
         self._h = handle
         self.n, self.m, self.directed = n, m, directed
+        self.device = device  # CUDA device index (None: not checked)
+
+    def _cuda(self) -> str:
+        """Where outputs the binding allocates go: the graph's device."""
+        return "cuda" if self.device is None else f"cuda:{self.device}"
 
     @classmethod
     def upload(cls, offsets, indices, directed: bool = False, transpose: bool = True,
@@ -181,8 +235,10 @@ class Graph:
         if ell:
             flags |= PG_ELL
         h = ctypes.c_void_p()
+        import torch
+        dev = torch.cuda.current_device()
         _check(lib.pg_graph_upload(po, pi, n, m, flags, _stream_ptr(stream), ctypes.byref(h)))
-        return cls(h, n, m, directed)
+        return cls(h, n, m, directed, device=dev)
 
     @classmethod
     def from_graphgen(cls, g, **kw) -> "Graph":
@@ -210,17 +266,18 @@ class Graph:
         """Exact hop distances from src; returns a CUDA int32 tensor (uint32 bits)."""
         import torch
         if out is None:
-            out = torch.empty(self.n, dtype=torch.int32, device="cuda")
-        ptr = ctypes.c_void_p(out.data_ptr()) if isinstance(out, torch.Tensor) else \
-            ctypes.c_void_p(out.ctypes.data)
+            out = torch.empty(self.n, dtype=torch.int32, device=self._cuda())
+        ptr = _buf(out, self.n, "bfs: out", _u32_types(), np.uint32, self.device)
         _check(load().pg_bfs(self._h, int(src), ptr, ctypes.byref(cfg) if cfg else None,
                              ctypes.byref(stats) if stats else None, _stream_ptr(stream)))
         return out
 
     def bfs_host(self, src: int, out: np.ndarray, cfg: Config | None = None, stream=None):
         """pg_bfs with a host output buffer (the library stages and copies back)."""
-        assert out.dtype == np.uint32 and out.flags.c_contiguous and len(out) == self.n
-        _check(load().pg_bfs(self._h, int(src), ctypes.c_void_p(out.ctypes.data),
+        if not isinstance(out, np.ndarray):
+            raise ValueError("bfs_host: out must be a numpy uint32 array")
+        ptr = _buf(out, self.n, "bfs_host: out", _u32_types(), np.uint32)
+        _check(load().pg_bfs(self._h, int(src), ptr,
                              ctypes.byref(cfg) if cfg else None, None, _stream_ptr(stream)))
         return out
 
@@ -229,8 +286,8 @@ class Graph:
         """Per-vertex uint64 source bitmasks (int64 CUDA tensors); (fwd, bwd)."""
         import torch
         src = np.ascontiguousarray(sources, dtype=np.uint32)
-        fwd = torch.empty(self.n, dtype=torch.int64, device="cuda") if direction & PG_FWD else None
-        bwd = torch.empty(self.n, dtype=torch.int64, device="cuda") if direction & PG_BWD else None
+        fwd = torch.empty(self.n, dtype=torch.int64, device=self._cuda()) if direction & PG_FWD else None
+        bwd = torch.empty(self.n, dtype=torch.int64, device=self._cuda()) if direction & PG_BWD else None
         _check(load().pg_reach_multi(self._h, ctypes.c_void_p(src.ctypes.data), len(src), direction,
                                      ctypes.c_void_p(fwd.data_ptr() if fwd is not None else 0),
                                      ctypes.c_void_p(bwd.data_ptr() if bwd is not None else 0),
@@ -244,12 +301,10 @@ class Graph:
         import torch
         src = np.ascontiguousarray(sources, dtype=np.uint32)
         if out is None:
-            out = torch.empty((len(src), self.n), dtype=torch.int32, device="cuda")
-        elif not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.int32
-                  and out.is_contiguous() and out.numel() >= len(src) * self.n):
-            raise ValueError("out must be a contiguous CUDA int32 tensor of k * n elements")
-        _check(load().pg_bfs_multi(self._h, ctypes.c_void_p(src.ctypes.data), len(src),
-                                   ctypes.c_void_p(out.data_ptr()),
+            out = torch.empty((len(src), self.n), dtype=torch.int32, device=self._cuda())
+        ptr = _buf(out, len(src) * self.n, "bfs_multi: out", _u32_types(), np.uint32, self.device,
+                   cuda_only=True)
+        _check(load().pg_bfs_multi(self._h, ctypes.c_void_p(src.ctypes.data), len(src), ptr,
                                    ctypes.byref(cfg) if cfg else None,
                                    ctypes.byref(stats) if stats else None, _stream_ptr(stream)))
         return out
@@ -259,12 +314,9 @@ class Graph:
         tensor (uint32 bits), and the number of pivot iterations."""
         import torch
         if out is None:
-            out = torch.empty(self.n, dtype=torch.int32, device="cuda")
-        if isinstance(out, np.ndarray):  # host output: the library stages and copies back
-            assert out.dtype == np.uint32 and out.flags.c_contiguous and len(out) == self.n
-            ptr = ctypes.c_void_p(out.ctypes.data)
-        else:
-            ptr = ctypes.c_void_p(out.data_ptr())
+            out = torch.empty(self.n, dtype=torch.int32, device=self._cuda())
+        # a host output (numpy array) is staged and copied back by the library
+        ptr = _buf(out, self.n, "scc: out", _u32_types(), np.uint32, self.device)
         it = ctypes.c_uint32()
         _check(load().pg_scc(self._h, ptr, ctypes.byref(cfg) if cfg else None,
                              ctypes.byref(stats) if stats else None, ctypes.byref(it), _stream_ptr(stream)))
@@ -285,33 +337,30 @@ class Graph:
         int64 tensor holding uint64 bits (0xFFFFFFFFFFFFFFFF: unreachable)."""
         import torch
         if out is None:
-            out = torch.empty(self.n, dtype=torch.int64, device="cuda")
-        if isinstance(out, torch.Tensor):
-            if out.dtype != torch.int64 or not out.is_contiguous() or out.numel() != self.n:
-                raise ValueError("sssp: out must be a contiguous int64 tensor of n entries")
-            ptr = ctypes.c_void_p(out.data_ptr())
-        else:
-            assert out.dtype == np.uint64 and out.flags.c_contiguous and len(out) == self.n
-            ptr = ctypes.c_void_p(out.ctypes.data)
+            out = torch.empty(self.n, dtype=torch.int64, device=self._cuda())
+        ptr = _buf(out, self.n, "sssp: out", _u64_types(), np.uint64, self.device)
         _check(load().pg_sssp(self._h, int(src), ptr, ctypes.byref(cfg) if cfg else None,
                               ctypes.byref(stats) if stats else None, _stream_ptr(stream)))
         return out
 
     def count_reached(self, dist, stream=None):
+        """(n_r, m_r) of a device distance vector: reached vertices and the
+        sum of their out-degrees."""
+        ptr = _buf(dist, self.n, "count_reached: dist", _u32_types(), np.uint32, self.device,
+                   cuda_only=True, writes=False)
         a, b = ctypes.c_uint64(), ctypes.c_uint64()
-        _check(load().pg_count_reached(self._h, ctypes.c_void_p(dist.data_ptr()), ctypes.byref(a),
+        _check(load().pg_count_reached(self._h, ptr, ctypes.byref(a),
                                        ctypes.byref(b), _stream_ptr(stream)))
         return a.value, b.value
 
     def set_transpose(self, t_offsets, t_indices, stream=None):
         """Replace the reversed CSR (host numpy arrays or CUDA tensors, uint32)."""
         ptrs = []
-        for a in (t_offsets, t_indices):
+        for a, count, what in ((t_offsets, self.n + 1, "set_transpose: t_offsets"),
+                               (t_indices, self.m, "set_transpose: t_indices")):
             if isinstance(a, np.ndarray):
                 a = np.ascontiguousarray(a, dtype=np.uint32)
-                ptrs.append((a, ctypes.c_void_p(a.ctypes.data)))
-            else:
-                ptrs.append((a, ctypes.c_void_p(a.data_ptr())))
+            ptrs.append((a, _buf(a, count, what, _u32_types(), np.uint32, self.device, writes=False)))
         _check(load().pg_graph_set_transpose(self._h, ptrs[0][1], ptrs[1][1], _stream_ptr(stream)))
 
     def set_schedule_weights(self, w):
@@ -337,29 +386,51 @@ def to_uint64(t) -> np.ndarray:
 
 
 # ------------------------------------------------------------- MLP kernels
+PG_MLP_IN = 5
+
+
+def _mlp_inputs(params, X):
+    """Shape, type and device checks of the network's parameters and
+    feature rows (X: B x PG_MLP_IN fp32); returns (B, device index)."""
+    if not (hasattr(X, "dim") and X.dim() == 2 and X.shape[1] == PG_MLP_IN):
+        raise ValueError(f"X must be a B x {PG_MLP_IN} tensor")
+    dev = X.device.index
+    _buf(params, PG_MLP_NPARAMS, "params", _f32_types(), np.float32, dev, cuda_only=True, writes=False)
+    _buf(X, X.shape[0] * PG_MLP_IN, "X", _f32_types(), np.float32, dev, cuda_only=True, writes=False)
+    return int(X.shape[0]), dev
+
+
 def mlp_forward(params, X, stream=None):
     import torch
-    Y = torch.empty((X.shape[0], PG_NUM_ACTIONS), dtype=torch.float32, device=X.device)
+    B, _ = _mlp_inputs(params, X)
+    Y = torch.empty((B, PG_NUM_ACTIONS), dtype=torch.float32, device=X.device)
     _check(load().pg_mlp_forward(ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(X.data_ptr()),
-                                 X.shape[0], ctypes.c_void_p(Y.data_ptr()), _stream_ptr(stream)))
+                                 B, ctypes.c_void_p(Y.data_ptr()), _stream_ptr(stream)))
     return Y
 
 
 def mlp_backward(params, X, act, target, stream=None):
     import torch
+    B, dev = _mlp_inputs(params, X)
+    pa = _buf(act, B, "act", _u32_types(), np.uint32, dev, cuda_only=True, writes=False)
+    pt = _buf(target, B, "target", _f32_types(), np.float32, dev, cuda_only=True, writes=False)
     grad = torch.empty(PG_MLP_NPARAMS, dtype=torch.float32, device=X.device)
     loss = torch.empty(1, dtype=torch.float32, device=X.device)
     _check(load().pg_mlp_backward(ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(X.data_ptr()),
-                                  ctypes.c_void_p(act.data_ptr()), ctypes.c_void_p(target.data_ptr()),
-                                  X.shape[0], ctypes.c_void_p(grad.data_ptr()),
+                                  pa, pt, B, ctypes.c_void_p(grad.data_ptr()),
                                   ctypes.c_void_p(loss.data_ptr()), _stream_ptr(stream)))
     return loss, grad
 
 
 def mlp_adam(params, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
-    _check(load().pg_mlp_adam(ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(grad.data_ptr()),
-                              ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(v.data_ptr()),
-                              params.numel(), t, lr, beta1, beta2, eps, _stream_ptr(stream)))
+    """One Adam step in place on params, m and v (fp32 CUDA tensors of the
+    same size as grad)."""
+    if not hasattr(params, "numel"):
+        raise ValueError("params must be a CUDA fp32 tensor")
+    count, dev = params.numel(), params.device.index
+    ptrs = [_buf(x, count, name, _f32_types(), np.float32, dev, cuda_only=True)
+            for x, name in ((params, "params"), (grad, "grad"), (m, "m"), (v, "v"))]
+    _check(load().pg_mlp_adam(*ptrs, count, t, lr, beta1, beta2, eps, _stream_ptr(stream)))
 
 
 def bfs_noalloc(offsets, indices, src: int, out, cfg: Config | None = None, stream=None):
