@@ -58,3 +58,14 @@ def test_algorithmic_bytes_of_one_bfs():
     59,569,914)."""
     b = _bench()
     assert b.algorithmic_bytes(10_000_000, 9_999_609, 59_569_914) == 318_278_096
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    """Under torchrun only rank 0 runs and prints the reference arm; another
+    rank exits 0 without work or output."""
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2",
+                        "--workload", "grid_1000", "--steps", "2", "--warmup", "1"], cwd=ROOT,
+                       capture_output=True, text=True, timeout=300, env=env)
+    assert r.returncode == 0, r.stderr
+    assert not [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
